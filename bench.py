@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Benchmark: 512^3-particle PM simulations (512^3 mesh, L = 1000 Mpc/h, CIC,
+6 BullFrog steps a = 0.02 -> 1), reported as PM particle-steps per second.
+
+One bench step = one full simulation: Zel'dovich ICs from resident white noise,
+6 DKD steps, and the final binned P(k) (FP64 bins read back to the host).
+value = N * 6 * K / (time of K steps) summed over ranks (replicas: every rank
+runs its own simulation; there is no data-path collective).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "512^3 PM particle-steps/s & %HBM roofline; batched serving p50/p99 latency"
+UNIT = "particle-steps/s"
+WORKLOAD = dict(workload="pm_512cubed_6step", n_part=512, n_mesh=512, box_mpc_h=1000.0, mass_assignment="CIC",
+                stepper="bullfrog", n_steps=6, a_ini=0.02, a_end=1.0, grad_order=4, lap_order=0,
+                pk_mesh=512, pk_bins=256, l2_policy="inputs larger than L2 (3.2 GB particle state, 3.7 GB workspace)")
+NOISE_SEED = 3
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(n_part, n_mesh):
+    """Compulsory HBM bytes per launch of each phase (float32; M = mesh cells,
+    N = particles; complex half spectra count as M/2 complex = 4M bytes)."""
+    N, M = n_part ** 3, n_mesh ** 3
+    return {
+        "deposit": 24 * N + 4 * M,               # read disp, vel; write the density once
+        "fft_x_fwd": 4 * M + 4 * M,              # read real mesh, write half spectrum
+        "fft_y_fwd": 8 * M,                      # read + write half spectrum
+        "fft_z_green": 4 * M + 12 * M,           # read 1 spectrum, write 3
+        "fft_y_inv": 3 * 8 * M,                  # 3 spectra in place
+        "fft_x_inv": 12 * M + 12 * M,            # 3 spectra -> 3 real force meshes
+        "interp_kick_drift": 48 * N + 12 * M,    # read disp, vel, 3 force meshes; write disp, vel
+    }
+
+
+def run_reference(args, ws, rank):
+    """The oracle (FP64 numpy, as it stands) on the host cores: each step is one
+    DKD step of a 128^3-particle sample of the same workload (128^3 mesh,
+    L = 250 Mpc/h keeps the 1.95 Mpc/h cell)."""
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import cosmology, nbody
+    from paper_2510_05206_gb300 import inputs
+
+    n = 128
+    cfg = nbody.Config(n_part=n, n_mesh=n, box=1000.0 * n / 512, n_steps=6)
+    tab = cosmology.step_table(cfg.get_growth(), cfg.a_ini, cfg.a_end, cfg.n_steps)
+    q = nbody.lattice(n, cfg.box)
+    P, V = nbody.zeldovich_ic(cfg, inputs.white_noise(n, NOISE_SEED))
+    for i in range(args.warmup):
+        P, V = nbody.step(cfg, P, V, tab[i % 6], q)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        P, V = nbody.step(cfg, P, V, tab[i % 6], q)
+    dt = time.perf_counter() - t0
+    value = n ** 3 * args.steps / dt
+    sample = f"{args.steps} DKD steps of a {n}^3-particle, {n}^3-mesh run (L = {cfg.box:g} Mpc/h), numpy FP64"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": WORKLOAD,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """Oracle timing on the host (rank 0, N = 1): ICs + 2 DKD steps at 128^3."""
+    from oracle import cosmology, nbody
+    from paper_2510_05206_gb300 import inputs
+    n = 128
+    cfg = nbody.Config(n_part=n, n_mesh=n, box=1000.0 * n / 512, n_steps=6)
+    tab = cosmology.step_table(cfg.get_growth(), cfg.a_ini, cfg.a_end, cfg.n_steps)
+    q = nbody.lattice(n, cfg.box)
+    w = inputs.white_noise(n, NOISE_SEED)
+    t0 = time.perf_counter()
+    P, V = nbody.zeldovich_ic(cfg, w)
+    for i in range(2):
+        P, V = nbody.step(cfg, P, V, tab[i], q)
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Zel'dovich ICs + 2 DKD steps at {n}^3 particles / {n}^3 mesh, L = {cfg.box:g} Mpc/h "
+                      f"(numpy FP64, single thread; {dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--size", type=int, default=512, help="particles per dimension (512 = the benchmark workload)")
+    ap.add_argument("--mesh", type=int, default=0, help="mesh cells per dimension (default = --size)")
+    args = ap.parse_args()
+    if args.size != 512 or (args.mesh and args.mesh != 512):
+        # a reduced case for profiling captures; the config says so
+        m = args.mesh or args.size
+        WORKLOAD.update(workload=f"pm_{args.size}cubed_on_{m}cubed_6step_profiling_case", n_part=args.size,
+                        n_mesh=m, box_mpc_h=1000.0 * m / 512, pk_mesh=m, pk_bins=m // 2)
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2510_05206_gb300 import PM, Config
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    n = WORKLOAD["n_part"]
+    cfg = Config(n_part=n, n_mesh=WORKLOAD["n_mesh"], box=WORKLOAD["box_mpc_h"], order=2, n_steps=6,
+                 a_ini=0.02, a_end=1.0, pk_mesh_max=WORKLOAD["pk_mesh"])
+    pm = PM(cfg, device=dev)
+    N = n ** 3
+    rng = np.random.default_rng(NOISE_SEED + rank)
+    noise_host = torch.from_numpy(rng.standard_normal(N, dtype=np.float32).reshape(1, N)).pin_memory()
+    noise = noise_host.to(dev)
+    disp, vel = pm.new_state()
+
+    def one_sim():
+        pm.ic_zeldovich(noise, disp, vel)
+        pm.run(disp, vel)
+        return pm.power_spectrum(disp, WORKLOAD["pk_mesh"], WORKLOAD["pk_bins"])
+
+    for _ in range(max(args.warmup, 3)):
+        one_sim()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    pm.profile(True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        k, pk, cnt = one_sim()
+    t1.record()
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    prof = pm.profile_read()
+    pm.profile(False)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    particle_steps = N * cfg.n_steps * args.steps * ws
+    value = particle_steps / (ms / 1e3)
+
+    # end to end through the host-buffer C ABI call: pinned noise in, disp + vel out
+    e2e = None
+    if args.e2e_steps > 0:
+        d_host = torch.empty((1, 3, N), dtype=torch.float32, pin_memory=True)
+        v_host = torch.empty((1, 3, N), dtype=torch.float32, pin_memory=True)
+        pm.simulate_host(noise_host, d_host, v_host)
+        if ws > 1:
+            dist.barrier()
+        te = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            pm.simulate_host(noise_host, d_host, v_host)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - te
+        if ws > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": N * cfg.n_steps * args.e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+               "d2h_bytes_per_step": 2 * 3 * 4 * N, "steps": args.e2e_steps,
+               "ms_per_step": e2e_s * 1e3 / args.e2e_steps}
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    alg = algorithmic_bytes(n, cfg.n_mesh)
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    for name, p in prof.items():
+        if p["calls"] == 0:
+            continue
+        per = p["ms"] / p["calls"]
+        entry = {"ms_per_launch": per, "launches": p["calls"], "share": p["ms"] / ms}
+        if name in alg:
+            entry["gbs"] = alg[name] / (per / 1e3) / 1e9
+            entry["frac"] = entry["gbs"] / peak
+        kernels[name] = entry
+    dom = max((k for k in kernels if k in alg), key=lambda k: kernels[k]["share"])
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kernels[dom]["frac"], "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+            "algorithmic_bytes_per_launch": alg[dom]}
+    launches = sum(p["launches"] for p in prof.values())
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": WORKLOAD, "roofline": roof, "kernels": kernels, "gpu_launches": int(launches),
+            "e2e": e2e,
+            "clocks": clock_info,
+            "ms_per_pm_step": ms / args.steps / cfg.n_steps}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pm.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

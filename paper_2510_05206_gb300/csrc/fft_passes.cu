@@ -1,0 +1,415 @@
+// Spectral passes of the PM force evaluation (Sec. 2.5, "Computing the forces"):
+//   x pass   real rows <-> half-spectrum rows (R2C / C2R via a half-length complex FFT)
+//   y pass   complex columns along y, in place
+//   z pass   complex columns along z, fused with the Fourier-space operator:
+//            force  (Poisson Green's function x gradient kernel, Table 2), 1 -> 3 spectra
+//            force with an interlaced grid (Sec. 2.8), 2 -> 6 spectra
+//            IC     (Zel'dovich displacement from white noise), 1 -> 3 spectra
+//            P(k)   (binned |delta_k|^2 with FP64 per-bin sums), 1 -> bins
+//            adjoint of the force operator (multiplier conj(m_c), summed), 3 -> 1
+// Transforms are unnormalised; normalisations are folded into the multipliers.
+#include "fft_core.cuh"
+#include "pm_kernels.h"
+
+namespace {
+
+using namespace pmfft;
+
+// ---------------------------------------------------------------- x pass, R2C
+// z[m] = x[2m] + i x[2m+1], Z = FFT_{n/2}(z),
+// X[k] = (Z[k] + conj Z[n/2-k]) / 2 - i/2 exp(-2 pi i k / n) (Z[k] - conj Z[n/2-k]),  k = 0..n/2.
+template <int LOG2N>
+__global__ void __launch_bounds__(256) k_fft_x_r2c(const float* __restrict__ in, long long in_stride,
+                                                   float2* __restrict__ out, long long out_stride,
+                                                   const float2* __restrict__ twg) {
+    constexpr int n = 1 << LOG2N, N = n / 2, P = N + SPEC_PAD;
+    constexpr int ROWS = (2048 / N) < n * n ? (2048 / N) : n * n;
+    constexpr int LS = N + 1;
+    extern __shared__ float2 sm[];
+    float2* tile = sm;
+    float2* tw = sm + ROWS * LS;
+    const int q = blockIdx.y;
+    const long long row0 = (long long)blockIdx.x * ROWS;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    const float4* src = reinterpret_cast<const float4*>(in + q * in_stride + row0 * n);
+    for (int i = threadIdx.x; i < ROWS * N / 2; i += blockDim.x) {
+        const int r = i / (N / 2), c = i % (N / 2);
+        const float4 v = src[i];
+        tile[r * LS + 2 * c] = make_float2(v.x, v.y);
+        tile[r * LS + 2 * c + 1] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+    fft_lines<N, ROWS, LS, 1, -1>(tile, tw, 2);
+    float2* dst = out + q * out_stride + row0 * P;
+    for (int i = threadIdx.x; i < ROWS * (N + 1); i += blockDim.x) {
+        const int r = i / (N + 1), k = i % (N + 1);
+        const float2 zk = tile[r * LS + (k == N ? 0 : k)];
+        const float2 zc = cconj(tile[r * LS + (k == 0 ? 0 : N - k)]);
+        const float2 e = cscale(cadd(zk, zc), 0.5f);
+        const float2 o = cmul_i(cscale(csub(zk, zc), 0.5f), -1);   // (Z - conj)/(2i)
+        dst[r * P + k] = cadd(e, cmul(tw[k], o));
+    }
+}
+
+// ---------------------------------------------------------------- x pass, C2R
+// Z[k] = X[k] + conj X[n/2-k] + i (X[k] - conj X[n/2-k]) exp(+2 pi i k / n), k < n/2;
+// z = IFFT_{n/2}(Z) (unnormalised) gives x[2m] = Re z[m], x[2m+1] = Im z[m].
+// EPI 0: out = x.  EPI 1: out = x, out2 = scale2 * x (Zel'dovich: V = psi1, Psi = D psi1).
+template <int LOG2N, int EPI>
+__global__ void __launch_bounds__(256) k_fft_x_c2r(const float2* __restrict__ in, long long in_stride,
+                                                   float* __restrict__ out, long long out_stride,
+                                                   float* __restrict__ out2, long long out2_stride,
+                                                   float scale2, const float2* __restrict__ twg) {
+    constexpr int n = 1 << LOG2N, N = n / 2, P = N + SPEC_PAD;
+    constexpr int ROWS = (2048 / N) < n * n ? (2048 / N) : n * n;
+    constexpr int LS = N + 1;
+    extern __shared__ float2 sm[];
+    float2* tile = sm;
+    float2* tw = sm + ROWS * LS;
+    const int q = blockIdx.y;
+    const long long row0 = (long long)blockIdx.x * ROWS;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    const float2* src = in + q * in_stride + row0 * P;
+    for (int i = threadIdx.x; i < ROWS * (N + 1); i += blockDim.x) {
+        const int r = i / (N + 1), k = i % (N + 1);
+        tile[r * LS + k] = src[r * P + k];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ROWS * (N / 2 + 1); i += blockDim.x) {
+        const int r = i / (N / 2 + 1), k = i % (N / 2 + 1);
+        float2* t = tile + r * LS;
+        const float2 a = t[k], b = t[N - k];
+        // Z[k]
+        const float2 ek = cadd(a, cconj(b));
+        const float2 ok = cmul(csub(a, cconj(b)), cconj(tw[k]));
+        const float2 zk = cadd(ek, cmul_i(ok, 1));
+        if (k > 0 && k < N / 2) {
+            const float2 em = cadd(b, cconj(a));
+            const float2 om = cmul(csub(b, cconj(a)), cconj(tw[N - k]));
+            t[N - k] = cadd(em, cmul_i(om, 1));
+        }
+        t[k] = zk;
+    }
+    __syncthreads();
+    fft_lines<N, ROWS, LS, 1, 1>(tile, tw, 2);
+    float4* dst = reinterpret_cast<float4*>(out + q * out_stride + row0 * n);
+    float4* dst2 = EPI == 1 ? reinterpret_cast<float4*>(out2 + q * out2_stride + row0 * n) : nullptr;
+    for (int i = threadIdx.x; i < ROWS * N / 2; i += blockDim.x) {
+        const int r = i / (N / 2), c = i % (N / 2);
+        const float2 z0 = tile[r * LS + 2 * c], z1 = tile[r * LS + 2 * c + 1];
+        const float4 v = make_float4(z0.x, z0.y, z1.x, z1.y);
+        dst[i] = v;
+        if (EPI == 1) dst2[i] = make_float4(scale2 * v.x, scale2 * v.y, scale2 * v.z, scale2 * v.w);
+    }
+}
+
+// ---------------------------------------------------------------- column tiles
+// A tile is COL_TILE adjacent kx columns of one (z) plane (y pass) or one (y) row
+// (z pass), all n elements along the transform axis; element e of column l
+// sits at tile[e * COL_TILE + l].
+template <int n>
+__device__ __forceinline__ void load_cols(float2* tile, const float2* __restrict__ base, long long estride) {
+    constexpr int Q = COL_TILE / 2;   // float4 per element row
+    for (int i = threadIdx.x; i < n * Q; i += blockDim.x) {
+        const int e = i / Q, c = i % Q;
+        const float4 v = reinterpret_cast<const float4*>(base + e * estride)[c];
+        tile[e * COL_TILE + 2 * c] = make_float2(v.x, v.y);
+        tile[e * COL_TILE + 2 * c + 1] = make_float2(v.z, v.w);
+    }
+}
+
+template <int n>
+__device__ __forceinline__ void store_cols(const float2* tile, float2* __restrict__ base, long long estride) {
+    constexpr int Q = COL_TILE / 2;
+    for (int i = threadIdx.x; i < n * Q; i += blockDim.x) {
+        const int e = i / Q, c = i % Q;
+        const float2 a = tile[e * COL_TILE + 2 * c], b = tile[e * COL_TILE + 2 * c + 1];
+        reinterpret_cast<float4*>(base + e * estride)[c] = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+// y pass: grid (tiles, n planes, meshes)
+template <int LOG2N, int DIR>
+__global__ void __launch_bounds__(1 << LOG2N) k_fft_y(float2* __restrict__ data, long long stride,
+                                                      const float2* __restrict__ twg) {
+    constexpr int n = 1 << LOG2N, P = n / 2 + SPEC_PAD;
+    extern __shared__ float2 sm[];
+    float2* tile = sm;
+    float2* tw = sm + n * COL_TILE;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    float2* base = data + blockIdx.z * stride + (long long)blockIdx.y * n * P + blockIdx.x * COL_TILE;
+    load_cols<n>(tile, base, P);
+    __syncthreads();
+    fft_lines<n, COL_TILE, 1, COL_TILE, DIR>(tile, tw, 1);
+    store_cols<n>(tile, base, P);
+}
+
+// ---------------------------------------------------------------- z pass
+struct ZArgs {
+    const float2* in[3];      // input spectra (slot 0); slot b adds b * slot_stride
+    float2* out[6];           // output spectra
+    long long slot_stride;    // complex elements between slots of one spectrum buffer
+    const float2* tw;         // exp(-2 pi i m / n), m < n
+    const float* lap1;        // 1D Laplacian kernel per bin (Table 2)
+    const float* grad1;       // Im of the 1D gradient kernel per bin, 0 on the Nyquist bin
+    const float* ictab;       // IC: sqrt(P(k) M / L^3) / (D(1) k^2) / M per integer k^2 index (0 if masked)
+    const int* bintab;        // P(k): bin of each integer k^2 index (-1 = none)
+    double* pk_out;           // P(k): [slot][3][nbins] (sum w|d|^2, sum w|k|, sum w)
+    int nbins;
+    float scale;              // overall factor of the multiplier
+    float kf;                 // 2 pi / L
+};
+
+enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4 };
+
+template <int LOG2N, int MODE>
+__global__ void __launch_bounds__(1 << LOG2N) k_fft_z(ZArgs a) {
+    constexpr int n = 1 << LOG2N, P = n / 2 + SPEC_PAD;
+    constexpr int T = n * COL_TILE;
+    constexpr long long ES = (long long)n * P;      // z stride (complex)
+    extern __shared__ float2 sm[];
+    float2* A = sm;                  // transformed input (forward along z)
+    float2* B = sm + T;              // work tile
+    float2* A2 = sm + 2 * T;         // second input (interlaced / adjoint)
+    float2* tw = sm + (MODE == Z_FORCE_IL || MODE == Z_ADJ ? 3 : 2) * T;
+    float* lap = reinterpret_cast<float*>(tw + n);
+    float* grad = lap + n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tw[i] = a.tw[i];
+        if (MODE != Z_IC && MODE != Z_PK) { lap[i] = a.lap1[i]; grad[i] = a.grad1[i]; }
+    }
+    const int slot = blockIdx.z;
+    const int y = blockIdx.y;
+    const int kx0 = blockIdx.x * COL_TILE;
+    const long long off = slot * a.slot_stride + (long long)y * P + kx0;
+    const int my = freq_index(y, n);
+
+    if (MODE == Z_ADJ) {
+        // sum_c conj(m_c) x_c^ ; m_c = -i D1(k_c) / K_lap(k) * scale  => conj(m_c) = +i D1 / K * scale
+        load_cols<n>(A, a.in[0] + off, ES);
+        __syncthreads();
+        fft_lines<n, COL_TILE, 1, COL_TILE, -1>(A, tw, 1);
+        for (int c = 1; c < 3; ++c) {
+            float2* X = c == 1 ? B : A2;
+            load_cols<n>(X, a.in[c] + off, ES);
+            __syncthreads();
+            fft_lines<n, COL_TILE, 1, COL_TILE, -1>(X, tw, 1);
+        }
+        for (int i = threadIdx.x; i < T; i += blockDim.x) {
+            const int e = i / COL_TILE, l = i % COL_TILE;
+            const int kx = kx0 + l;
+            float2 r = make_float2(0.f, 0.f);
+            if (kx <= n / 2 && (kx | y | e)) {
+                const float inv = a.scale / (lap[kx] + lap[y] + lap[e]);
+                // +i * (gx A + gy B + gz A2) * inv
+                const float2 s = cadd(cadd(cscale(A[i], grad[kx]), cscale(B[i], grad[y])), cscale(A2[i], grad[e]));
+                r = cmul_i(cscale(s, inv), 1);
+            }
+            A[i] = r;
+        }
+        __syncthreads();
+        fft_lines<n, COL_TILE, 1, COL_TILE, 1>(A, tw, 1);
+        store_cols<n>(A, a.out[0] + off, ES);
+        return;
+    }
+
+    load_cols<n>(A, a.in[0] + off, ES);
+    if (MODE == Z_FORCE_IL) load_cols<n>(A2, a.in[1] + off, ES);
+    __syncthreads();
+    fft_lines<n, COL_TILE, 1, COL_TILE, -1>(A, tw, 1);
+    if (MODE == Z_FORCE_IL) fft_lines<n, COL_TILE, 1, COL_TILE, -1>(A2, tw, 1);
+
+    if (MODE == Z_PK) {
+        // per-CTA FP64 bin sums in shared memory, then one global atomic per bin
+        double* acc = reinterpret_cast<double*>(B);     // 3 * nbins doubles (<= T float2)
+        for (int i = threadIdx.x; i < 3 * a.nbins; i += blockDim.x) acc[i] = 0.0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < T; i += blockDim.x) {
+            const int e = i / COL_TILE, l = i % COL_TILE;
+            const int kx = kx0 + l;
+            if (kx > n / 2) continue;
+            const int mz = freq_index(e, n);
+            const int s = kx * kx + my * my + mz * mz;
+            const int b = a.bintab[s];
+            if (b < 0) continue;
+            const double w = (kx == 0 || kx == n / 2) ? 1.0 : 2.0;
+            const double re = A[i].x, im = A[i].y;
+            atomicAdd(&acc[b], w * (re * re + im * im));
+            atomicAdd(&acc[a.nbins + b], w * sqrt((double)s));
+            atomicAdd(&acc[2 * a.nbins + b], w);
+        }
+        __syncthreads();
+        double* dst = a.pk_out + (long long)slot * 3 * a.nbins;
+        for (int i = threadIdx.x; i < 3 * a.nbins; i += blockDim.x)
+            if (acc[i] != 0.0) atomicAdd(&dst[i], acc[i]);
+        return;
+    }
+
+    const int ncomp = MODE == Z_FORCE_IL ? 6 : 3;
+    for (int c = 0; c < ncomp; ++c) {
+        const int axis = c % 3;
+        for (int i = threadIdx.x; i < T; i += blockDim.x) {
+            const int e = i / COL_TILE, l = i % COL_TILE;
+            const int kx = kx0 + l;
+            float2 r = make_float2(0.f, 0.f);
+            if (kx <= n / 2) {
+                const int mz = freq_index(e, n);
+                if (MODE == Z_IC) {
+                    // psi1_c^ = i k_c T(k^2) w^, zero on every Nyquist plane
+                    if (kx != n / 2 && y != n / 2 && e != n / 2) {
+                        const int s = kx * kx + my * my + mz * mz;
+                        const int mc = axis == 0 ? kx : (axis == 1 ? my : mz);
+                        const float f = a.kf * (float)mc * __ldg(&a.ictab[s]);
+                        r = cmul_i(cscale(A[i], f), 1);
+                    }
+                } else {
+                    // g_c^ = -i D1(k_c) / K_lap(k) * scale * delta^   (k = 0 -> 0)
+                    const int bc = axis == 0 ? kx : (axis == 1 ? y : e);
+                    float2 d = A[i];
+                    bool keep = (kx | y | e) != 0;
+                    if (MODE == Z_FORCE_IL) {
+                        // delta^ = (d0^ + exp(i k.s) d1^) / 2, s = H/2 (1,1,1); every Nyquist plane zeroed
+                        keep = keep && kx != n / 2 && y != n / 2 && e != n / 2;
+                        const float ph = 3.14159265358979f / n * (float)(kx + my + mz);
+                        float sn, cs;
+                        sincosf(ph, &sn, &cs);
+                        d = cscale(cadd(d, cmul(make_float2(cs, sn), A2[i])), 0.5f);
+                        if (c >= 3) d = cmul(d, make_float2(cs, -sn));   // grid 1: g^ exp(-i k.s)
+                    }
+                    if (keep) {
+                        const float f = -grad[bc] * a.scale / (lap[kx] + lap[y] + lap[e]);
+                        r = cmul_i(cscale(d, f), 1);
+                    }
+                }
+            }
+            B[i] = r;
+        }
+        __syncthreads();
+        fft_lines<n, COL_TILE, 1, COL_TILE, 1>(B, tw, 1);
+        store_cols<n>(B, a.out[c] + off, ES);
+        __syncthreads();
+    }
+}
+
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int LOG2N>
+int rows_per_cta() {
+    constexpr int n = 1 << LOG2N, N = n / 2;
+    return (2048 / N) < n * n ? (2048 / N) : n * n;
+}
+
+template <int LOG2N>
+void launch_x_r2c(const float* in, long long in_stride, float2* out, long long out_stride, int nmesh,
+                  const float2* tw, cudaStream_t st) {
+    constexpr int n = 1 << LOG2N, N = n / 2;
+    const int rows = rows_per_cta<LOG2N>();
+    const size_t smem = (size_t)(rows * (N + 1) + n) * sizeof(float2);
+    set_smem(k_fft_x_r2c<LOG2N>, smem);
+    dim3 grid(n * n / rows, nmesh);
+    k_fft_x_r2c<LOG2N><<<grid, 256, smem, st>>>(in, in_stride, out, out_stride, tw);
+}
+
+template <int LOG2N>
+void launch_x_c2r(const float2* in, long long in_stride, float* out, long long out_stride, float* out2,
+                  long long out2_stride, float scale2, int nmesh, const float2* tw, cudaStream_t st) {
+    constexpr int n = 1 << LOG2N, N = n / 2;
+    const int rows = rows_per_cta<LOG2N>();
+    const size_t smem = (size_t)(rows * (N + 1) + n) * sizeof(float2);
+    dim3 grid(n * n / rows, nmesh);
+    if (out2) {
+        set_smem(k_fft_x_c2r<LOG2N, 1>, smem);
+        k_fft_x_c2r<LOG2N, 1><<<grid, 256, smem, st>>>(in, in_stride, out, out_stride, out2, out2_stride, scale2, tw);
+    } else {
+        set_smem(k_fft_x_c2r<LOG2N, 0>, smem);
+        k_fft_x_c2r<LOG2N, 0><<<grid, 256, smem, st>>>(in, in_stride, out, out_stride, out2, out2_stride, scale2, tw);
+    }
+}
+
+template <int LOG2N>
+void launch_y(float2* data, long long stride, int nmesh, int dir, const float2* tw, cudaStream_t st) {
+    constexpr int n = 1 << LOG2N;
+    const size_t smem = (size_t)(n * COL_TILE + n) * sizeof(float2);
+    dim3 grid(n / 2 / COL_TILE + 1, n, nmesh);
+    if (dir < 0) {
+        set_smem(k_fft_y<LOG2N, -1>, smem);
+        k_fft_y<LOG2N, -1><<<grid, n, smem, st>>>(data, stride, tw);
+    } else {
+        set_smem(k_fft_y<LOG2N, 1>, smem);
+        k_fft_y<LOG2N, 1><<<grid, n, smem, st>>>(data, stride, tw);
+    }
+}
+
+template <int LOG2N, int MODE>
+void launch_z_mode(const ZArgs& a, int nslots, cudaStream_t st) {
+    constexpr int n = 1 << LOG2N;
+    const int ntile = (MODE == Z_FORCE_IL || MODE == Z_ADJ) ? 3 : 2;
+    const size_t smem = (size_t)(ntile * n * COL_TILE + n) * sizeof(float2) + 2 * n * sizeof(float);
+    dim3 grid(n / 2 / COL_TILE + 1, n, nslots);
+    set_smem(k_fft_z<LOG2N, MODE>, smem);
+    k_fft_z<LOG2N, MODE><<<grid, n, smem, st>>>(a);
+}
+
+template <int LOG2N>
+void launch_z(int mode, const ZArgs& a, int nslots, cudaStream_t st) {
+    switch (mode) {
+        case Z_FORCE: launch_z_mode<LOG2N, Z_FORCE>(a, nslots, st); break;
+        case Z_FORCE_IL: launch_z_mode<LOG2N, Z_FORCE_IL>(a, nslots, st); break;
+        case Z_IC: launch_z_mode<LOG2N, Z_IC>(a, nslots, st); break;
+        case Z_PK: launch_z_mode<LOG2N, Z_PK>(a, nslots, st); break;
+        case Z_ADJ: launch_z_mode<LOG2N, Z_ADJ>(a, nslots, st); break;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host dispatch
+#define PM_DISPATCH_LOG2N(L2, CALL)                 \
+    switch (L2) {                                   \
+        case 4: { constexpr int LG = 4; CALL; } break;  \
+        case 5: { constexpr int LG = 5; CALL; } break;  \
+        case 6: { constexpr int LG = 6; CALL; } break;  \
+        case 7: { constexpr int LG = 7; CALL; } break;  \
+        case 8: { constexpr int LG = 8; CALL; } break;  \
+        case 9: { constexpr int LG = 9; CALL; } break;  \
+        case 10: { constexpr int LG = 10; CALL; } break; \
+        default: return -1;                         \
+    }
+
+int pm_fft_r2c_x(int log2n, const float* in, long long in_stride, float2* out, long long out_stride, int nmesh,
+                 const float2* tw, cudaStream_t st) {
+    PM_DISPATCH_LOG2N(log2n, (launch_x_r2c<LG>(in, in_stride, out, out_stride, nmesh, tw, st)));
+    return 0;
+}
+
+int pm_fft_c2r_x(int log2n, const float2* in, long long in_stride, float* out, long long out_stride, float* out2,
+                 long long out2_stride, float scale2, int nmesh, const float2* tw, cudaStream_t st) {
+    PM_DISPATCH_LOG2N(log2n, (launch_x_c2r<LG>(in, in_stride, out, out_stride, out2, out2_stride, scale2, nmesh, tw, st)));
+    return 0;
+}
+
+int pm_fft_y(int log2n, float2* data, long long stride, int nmesh, int dir, const float2* tw, cudaStream_t st) {
+    PM_DISPATCH_LOG2N(log2n, (launch_y<LG>(data, stride, nmesh, dir, tw, st)));
+    return 0;
+}
+
+int pm_fft_z(int log2n, int mode, const PmZPass& p, int nslots, cudaStream_t st) {
+    ZArgs a;
+    for (int i = 0; i < 3; ++i) a.in[i] = p.in[i];
+    for (int i = 0; i < 6; ++i) a.out[i] = p.out[i];
+    a.slot_stride = p.slot_stride;
+    a.tw = p.tw;
+    a.lap1 = p.lap1;
+    a.grad1 = p.grad1;
+    a.ictab = p.ictab;
+    a.bintab = p.bintab;
+    a.pk_out = p.pk_out;
+    a.nbins = p.nbins;
+    a.scale = p.scale;
+    a.kf = p.kf;
+    PM_DISPATCH_LOG2N(log2n, (launch_z<LG>(mode, a, nslots, st)));
+    return 0;
+}

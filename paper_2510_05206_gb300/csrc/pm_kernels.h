@@ -1,0 +1,50 @@
+// Host-side launchers of the PM kernels (internal to libpmgb; the public C ABI
+// is include/pmgb.h).  Every launcher enqueues on the given stream and returns
+// 0, or -1 for an unsupported size.
+#pragma once
+#include <cuda_runtime.h>
+#include "pm_common.cuh"
+
+struct PmZPass {
+    const float2* in[3];
+    float2* out[6];
+    long long slot_stride;
+    const float2* tw;
+    const float* lap1;
+    const float* grad1;
+    const float* ictab;
+    const int* bintab;
+    double* pk_out;
+    int nbins;
+    float scale;
+    float kf;
+};
+
+enum { PM_Z_FORCE = 0, PM_Z_FORCE_IL = 1, PM_Z_IC = 2, PM_Z_PK = 3, PM_Z_ADJ = 4 };
+
+int pm_fft_r2c_x(int log2n, const float* in, long long in_stride, float2* out, long long out_stride, int nmesh,
+                 const float2* tw, cudaStream_t st);
+int pm_fft_c2r_x(int log2n, const float2* in, long long in_stride, float* out, long long out_stride, float* out2,
+                 long long out2_stride, float scale2, int nmesh, const float2* tw, cudaStream_t st);
+int pm_fft_y(int log2n, float2* data, long long stride, int nmesh, int dir, const float2* tw, cudaStream_t st);
+int pm_fft_z(int log2n, int mode, const PmZPass& p, int nslots, cudaStream_t st);
+
+// Particle kernels.  Geometry shared by deposit and interpolation.
+struct PmGeom {
+    int log2np;          // particles per dimension = 1 << log2np
+    int log2ng;          // mesh cells per dimension = 1 << log2ng
+    float inv_h;         // 1 / H, H = L / n_mesh
+    long long slot_part; // floats between slots of one state component array (= 3 N)
+    long long slot_mesh; // floats between slots of the mesh array passed (M per mesh x meshes per slot)
+};
+
+// rho[b] += sum_i W(r_j - X_i (+ shift)) for X = q + disp + tau1 * vel (vel may be null).
+int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, const SlotCoef* coef,
+               int coef_stride, float shift_cells, float* rho, int nslots, cudaStream_t st);
+// A = gather(g) / D_half^2 at X_half = q + disp + tau1 vel; V' = alpha V + kick A; disp' = disp + tau1 V + tau2 V'.
+// force: [slot][3 or 6][M] (6 with an interlaced second grid at +1/2 cell).
+int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float* vel, const SlotCoef* coef,
+                   int coef_stride, const float* force, int nslots, cudaStream_t st);
+// acc[b][c][i] = sum_j g_c,j W(r_j - X_i) at X = q + disp (no kick): stage-level interpolation.
+int pm_interp(int order, int interlace, const PmGeom& g, const float* disp, const float* force, float* acc,
+              int nslots, cudaStream_t st);

@@ -1,0 +1,212 @@
+"""Thin torch binding of libpmgb (include/pmgb.h): same names, argument
+marshalling only.  Every step of the PM path runs in the library's CUDA
+kernels; tensors only supply device memory and the current stream."""
+import ctypes
+from dataclasses import dataclass, fields
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+@dataclass
+class Config:
+    n_part: int = 64
+    n_mesh: int = 64
+    box: float = 256.0
+    order: int = 2
+    interlace: int = 0
+    grad_order: int = 4
+    lap_order: int = 0
+    omega_m: float = 0.3
+    h: float = 0.7
+    n_s: float = 0.96
+    sigma8: float = 0.8
+    a_ini: float = 0.02
+    a_end: float = 1.0
+    n_steps: int = 6
+    stepper: int = 0
+    time_var: int = 0
+    zero_corner: int = 1
+    batch: int = 1
+    pk_mesh_max: int = 0
+
+    def to_c(self):
+        c = _lib.PmConfig()
+        for f in fields(self):
+            setattr(c, f.name, getattr(self, f.name))
+        return c
+
+
+def workspace_bytes(cfg: Config) -> int:
+    lib = _lib.load()
+    out = ctypes.c_size_t()
+    c = cfg.to_c()
+    _lib.check(lib.pm_workspace_bytes(ctypes.byref(c), ctypes.byref(out)))
+    return out.value
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class PM:
+    """One libpmgb handle serving ``cfg.batch`` simulations of the same size."""
+
+    def __init__(self, cfg: Config, device="cuda"):
+        self.lib = _lib.load()
+        self.cfg = cfg
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("libpmgb runs on CUDA devices only")
+        torch.cuda.init()
+        with torch.cuda.device(self.device):
+            h = ctypes.c_void_p()
+            c = cfg.to_c()
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            _lib.check(self.lib.pm_init(ctypes.byref(c), ctypes.c_void_p(stream), ctypes.byref(h)))
+        self.h = h
+        self.N = cfg.n_part ** 3
+        self.B = cfg.batch
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ helpers
+    def _stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        _lib.check(self.lib.pm_set_stream(self.h, ctypes.c_void_p(s)), self.h)
+
+    def _check(self, rc):
+        _lib.check(rc, self.h)
+
+    def _state_ok(self, t, name, shape):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+        if t.numel() != int(np.prod(shape)):
+            raise ValueError(f"{name} has {t.numel()} elements, expected {shape}")
+
+    def new_state(self):
+        shape = (self.B, 3, self.N)
+        return (torch.zeros(shape, device=self.device, dtype=torch.float32),
+                torch.zeros(shape, device=self.device, dtype=torch.float32))
+
+    # ------------------------------------------------------------ API
+    def step_table(self):
+        out = np.zeros((self.cfg.n_steps, 7))
+        self._check(self.lib.pm_step_table(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           self.cfg.n_steps))
+        return out
+
+    def growth(self, a):
+        out = np.zeros(3)
+        self._check(self.lib.pm_growth(self.h, float(a), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def ic_zeldovich(self, noise, disp=None, vel=None):
+        self._state_ok(noise, "noise", (self.B, self.N))
+        if disp is None:
+            disp, vel = self.new_state()
+        self._state_ok(disp, "disp", (self.B, 3, self.N))
+        self._state_ok(vel, "vel", (self.B, 3, self.N))
+        self._stream()
+        self._check(self.lib.pm_ic_zeldovich(self.h, _ptr(noise), _ptr(disp), _ptr(vel)))
+        return disp, vel
+
+    def ic_zeldovich_slot(self, slot, noise, disp, vel):
+        self._stream()
+        self._check(self.lib.pm_ic_zeldovich_slot(self.h, int(slot), _ptr(noise), _ptr(disp), _ptr(vel)))
+
+    def step(self, disp, vel, step):
+        self._stream()
+        self._check(self.lib.pm_step(self.h, _ptr(disp), _ptr(vel), int(step)))
+
+    def run(self, disp, vel, begin=0, end=None):
+        self._state_ok(disp, "disp", (self.B, 3, self.N))
+        self._state_ok(vel, "vel", (self.B, 3, self.N))
+        self._stream()
+        end = self.cfg.n_steps if end is None else end
+        self._check(self.lib.pm_run(self.h, _ptr(disp), _ptr(vel), int(begin), int(end)))
+        return disp, vel
+
+    def set_slots(self, n_steps, step):
+        ns = np.ascontiguousarray(n_steps, dtype=np.int32)
+        st = np.ascontiguousarray(step, dtype=np.int32)
+        if ns.size != self.B or st.size != self.B:
+            raise ValueError("one entry per slot expected")
+        self._stream()
+        self._check(self.lib.pm_set_slots(self.h, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+
+    def step_slots(self, disp, vel):
+        self._stream()
+        self._check(self.lib.pm_step_slots(self.h, _ptr(disp), _ptr(vel)))
+
+    def power_spectrum(self, disp, n_mesh=None, n_bins=None):
+        n = n_mesh or (self.cfg.pk_mesh_max or self.cfg.n_mesh)
+        nb = n_bins or n // 2
+        k = np.zeros((self.B, nb))
+        pk = np.zeros((self.B, nb))
+        cnt = np.zeros((self.B, nb), dtype=np.int64)
+        self._stream()
+        self._check(self.lib.pm_power_spectrum(
+            self.h, _ptr(disp), int(n), int(nb), k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            pk.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return k, pk, cnt
+
+    def density(self, disp, n_mesh=None, order=None):
+        n = n_mesh or self.cfg.n_mesh
+        out = torch.empty((self.B, n, n, n), device=self.device, dtype=torch.float32)
+        self._stream()
+        self._check(self.lib.pm_density(self.h, _ptr(disp), int(n), int(order or self.cfg.order), _ptr(out)))
+        return out
+
+    def force_mesh(self, delta):
+        n = self.cfg.n_mesh
+        self._state_ok(delta, "delta", (self.B, n, n, n))
+        out = torch.empty((self.B, 3, n, n, n), device=self.device, dtype=torch.float32)
+        self._stream()
+        self._check(self.lib.pm_force_mesh(self.h, _ptr(delta), _ptr(out)))
+        return out
+
+    def interp(self, disp, force):
+        out = torch.empty((self.B, 3, self.N), device=self.device, dtype=torch.float32)
+        self._stream()
+        self._check(self.lib.pm_interp(self.h, _ptr(disp), _ptr(force), _ptr(out)))
+        return out
+
+    PHASES = ("deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv",
+              "interp_kick_drift", "ic_zeldovich", "power_spectrum", "reserved")
+
+    def profile(self, enable=True):
+        self._check(self.lib.pm_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        ms = np.zeros(10)
+        calls = np.zeros(10, dtype=np.int64)
+        launches = np.zeros(10, dtype=np.int64)
+        self._check(self.lib.pm_profile_read(self.h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             calls.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                             launches.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 10))
+        return {p: dict(ms=ms[i], calls=int(calls[i]), launches=int(launches[i])) for i, p in enumerate(self.PHASES)}
+
+    def simulate_host(self, noise, disp=None, vel=None):
+        """noise: host float32 array/tensor [B, N] (pinned for full speed); returns host disp, vel."""
+        if isinstance(noise, np.ndarray):
+            noise = torch.from_numpy(np.ascontiguousarray(noise, dtype=np.float32))
+        if disp is None:
+            disp = torch.empty((self.B, 3, self.N), dtype=torch.float32, pin_memory=True)
+            vel = torch.empty((self.B, 3, self.N), dtype=torch.float32, pin_memory=True)
+        self._stream()
+        self._check(self.lib.pm_simulate_host(self.h, ctypes.c_void_p(noise.data_ptr()),
+                                              ctypes.c_void_p(disp.data_ptr()), ctypes.c_void_p(vel.data_ptr())))
+        return disp, vel
