@@ -157,11 +157,35 @@ int pm_force_mesh(pm_handle* h, const float* delta, float* force);
  * sum_j force[slot][c][j] W(r_j - X_i), X = q + disp. */
 int pm_interp(pm_handle* h, const float* disp, const float* force, float* acc);
 
+/* Adjoint method (Sec. 2.7, Table 5) with the scatter/gather pullbacks of
+ * App. C, for every slot, in place and with memory independent of the number
+ * of steps: on entry (disp, vel) is the state after step_end steps and
+ * (adj_disp, adj_vel) = (dL/dPsi, dL/dV) there; steps step_end-1 .. 0 run
+ * backwards (primal drift back, adjoint drift, force recomputation, primal
+ * kick back, adjoint kick through the VJP of A, velocity cotangent rescale,
+ * drift back, adjoint drift).  On return (disp, vel) is the reintegrated
+ * initial state and (adj_disp, adj_vel) the cotangents of the initial state.
+ * Single grid only (interlace = 0, else PM_ERR_UNSUPPORTED).  Allocates three
+ * adjoint meshes per slot on its first call. */
+int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adj_disp, float* adj_vel, int32_t step_end);
+
+/* Pullback through the Zel'dovich initial conditions: with psi1* = D(a_ini)
+ * adj_disp + adj_vel, adj_noise = sum_c F_c^T psi1*_c (F_c: noise -> psi1_c);
+ * dsigma8 (host [slot], may be NULL) = <adj_noise, noise> / sigma8, since psi1
+ * is proportional to sigma8.  Synchronises the stream when dsigma8 != NULL. */
+int pm_ic_adjoint(pm_handle* h, const float* noise, const float* adj_disp, const float* adj_vel, float* adj_noise,
+                  double* dsigma8);
+
+/* Pullback of pm_density w.r.t. positions (App. C, scatter VJP w.r.t.
+ * positions): adj_disp = (M/N) sum_j dL_ddelta_j d/dX W(r_j - X) (overwritten). */
+int pm_density_vjp(pm_handle* h, const float* disp, int32_t n_mesh, int32_t order, const float* dL_ddelta,
+                   float* adj_disp);
+
 /* Phase timing.  enable != 0 starts recording a CUDA event pair around every
  * phase the handle enqueues (and resets the counters); 0 stops.  Phases:
  * 0 deposit, 1 forward x FFT, 2 forward y FFT, 3 z FFT with the Fourier-space
  * operator, 4 inverse y FFT, 5 inverse x FFT, 6 interpolation + kick + drift,
- * 7 Zel'dovich ICs, 8 P(k), 9 reserved.  Kernel launches are counted always. */
+ * 7 Zel'dovich ICs, 8 P(k), 9 adjoint spectral passes.  Kernel launches are counted always. */
 int pm_profile(pm_handle* h, int32_t enable);
 
 /* Synchronises the stream and returns, per phase (cap >= 10 entries), the summed

@@ -47,6 +47,9 @@ _SIGS = {
     "pm_density": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
     "pm_force_mesh": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pm_interp": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pm_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
+    "pm_ic_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
+    "pm_density_vjp": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
     "pm_profile": (c_int32, [c_void_p, c_int32]),
     "pm_profile_read": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), POINTER(c_int64), c_int32]),
     "pm_simulate_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),

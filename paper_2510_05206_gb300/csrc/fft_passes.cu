@@ -160,7 +160,7 @@ struct ZArgs {
     float kf;                 // 2 pi / L
 };
 
-enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4 };
+enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5 };
 
 template <int LOG2N, int MODE>
 __global__ void __launch_bounds__(1 << LOG2N) k_fft_z(ZArgs a) {
@@ -171,12 +171,12 @@ __global__ void __launch_bounds__(1 << LOG2N) k_fft_z(ZArgs a) {
     float2* A = sm;                  // transformed input (forward along z)
     float2* B = sm + T;              // work tile
     float2* A2 = sm + 2 * T;         // second input (interlaced / adjoint)
-    float2* tw = sm + (MODE == Z_FORCE_IL || MODE == Z_ADJ ? 3 : 2) * T;
+    float2* tw = sm + (MODE == Z_FORCE_IL || MODE == Z_ADJ || MODE == Z_IC_ADJ ? 3 : 2) * T;
     float* lap = reinterpret_cast<float*>(tw + n);
     float* grad = lap + n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         tw[i] = a.tw[i];
-        if (MODE != Z_IC && MODE != Z_PK) { lap[i] = a.lap1[i]; grad[i] = a.grad1[i]; }
+        if (MODE != Z_IC && MODE != Z_PK && MODE != Z_IC_ADJ) { lap[i] = a.lap1[i]; grad[i] = a.grad1[i]; }
     }
     const int slot = blockIdx.z;
     const int y = blockIdx.y;
@@ -184,8 +184,9 @@ __global__ void __launch_bounds__(1 << LOG2N) k_fft_z(ZArgs a) {
     const long long off = slot * a.slot_stride + (long long)y * P + kx0;
     const int my = freq_index(y, n);
 
-    if (MODE == Z_ADJ) {
-        // sum_c conj(m_c) x_c^ ; m_c = -i D1(k_c) / K_lap(k) * scale  => conj(m_c) = +i D1 / K * scale
+    if (MODE == Z_ADJ || MODE == Z_IC_ADJ) {
+        // Z_ADJ: sum_c conj(m_c) x_c^, m_c = -i D1(k_c) / K_lap(k) * scale => conj(m_c) = +i D1 / K * scale
+        // Z_IC_ADJ: sum_c conj(i k_c T(k^2)) x_c^ = -i T sum_c k_c x_c^ (every Nyquist plane zero)
         load_cols<n>(A, a.in[0] + off, ES);
         __syncthreads();
         fft_lines<n, COL_TILE, 1, COL_TILE, -1>(A, tw, 1);
@@ -199,11 +200,18 @@ __global__ void __launch_bounds__(1 << LOG2N) k_fft_z(ZArgs a) {
             const int e = i / COL_TILE, l = i % COL_TILE;
             const int kx = kx0 + l;
             float2 r = make_float2(0.f, 0.f);
-            if (kx <= n / 2 && (kx | y | e)) {
+            if (MODE == Z_ADJ && kx <= n / 2 && (kx | y | e)) {
                 const float inv = a.scale / (lap[kx] + lap[y] + lap[e]);
                 // +i * (gx A + gy B + gz A2) * inv
                 const float2 s = cadd(cadd(cscale(A[i], grad[kx]), cscale(B[i], grad[y])), cscale(A2[i], grad[e]));
                 r = cmul_i(cscale(s, inv), 1);
+            }
+            if (MODE == Z_IC_ADJ && kx < n / 2 && y != n / 2 && e != n / 2) {
+                const int mz = freq_index(e, n);
+                const int s2 = kx * kx + my * my + mz * mz;
+                const float f = a.kf * __ldg(&a.ictab[s2]);
+                const float2 s = cadd(cadd(cscale(A[i], (float)kx), cscale(B[i], (float)my)), cscale(A2[i], (float)mz));
+                r = cmul_i(cscale(s, f), -1);
             }
             A[i] = r;
         }
@@ -346,7 +354,7 @@ void launch_y(float2* data, long long stride, int nmesh, int dir, const float2* 
 template <int LOG2N, int MODE>
 void launch_z_mode(const ZArgs& a, int nslots, cudaStream_t st) {
     constexpr int n = 1 << LOG2N;
-    const int ntile = (MODE == Z_FORCE_IL || MODE == Z_ADJ) ? 3 : 2;
+    const int ntile = (MODE == Z_FORCE_IL || MODE == Z_ADJ || MODE == Z_IC_ADJ) ? 3 : 2;
     const size_t smem = (size_t)(ntile * n * COL_TILE + n) * sizeof(float2) + 2 * n * sizeof(float);
     dim3 grid(n / 2 / COL_TILE + 1, n, nslots);
     set_smem(k_fft_z<LOG2N, MODE>, smem);
@@ -361,6 +369,7 @@ void launch_z(int mode, const ZArgs& a, int nslots, cudaStream_t st) {
         case Z_IC: launch_z_mode<LOG2N, Z_IC>(a, nslots, st); break;
         case Z_PK: launch_z_mode<LOG2N, Z_PK>(a, nslots, st); break;
         case Z_ADJ: launch_z_mode<LOG2N, Z_ADJ>(a, nslots, st); break;
+        case Z_IC_ADJ: launch_z_mode<LOG2N, Z_IC_ADJ>(a, nslots, st); break;
     }
 }
 

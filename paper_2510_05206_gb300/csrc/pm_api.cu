@@ -64,6 +64,9 @@ struct pm_handle {
     cudaEvent_t slot_ev[4] = {};
     int slot_ring = 0;
     std::map<int, std::vector<pmcosmo::StepCoef>> tables_by_nsteps;
+    // adjoint scratch: 3 meshes per slot of max(Mg, Np) floats (allocated on first use)
+    float* adj3 = nullptr;
+    double* d_dot = nullptr;
     // host-buffer mode
     float *d_noise = nullptr, *d_disp = nullptr, *d_vel = nullptr;
     size_t bytes = 0;
@@ -483,6 +486,8 @@ void pm_destroy(pm_handle* h) {
     cudaFree(h->d_ictab);
     cudaFree(h->d_pk);
     for (auto& kv : h->d_bintab) cudaFree(kv.second);
+    cudaFree(h->adj3);
+    cudaFree(h->d_dot);
     cudaFree(h->d_noise);
     cudaFree(h->d_disp);
     cudaFree(h->d_vel);
@@ -683,6 +688,115 @@ int pm_interp(pm_handle* h, const float* disp, const float* force, float* acc) {
     if (h->ngrids != 1) return h->fail(PM_ERR_UNSUPPORTED, "pm_interp: single grid only");
     pm_interp(h->cfg.order, 0, geom(h, h->ng, 3 * h->Mg()), disp, force, acc, h->B, h->stream);
     return h->check_launch("pm_interp");
+}
+
+namespace {
+int adj_alloc(pm_handle* h) {
+    if (h->adj3) return PM_OK;
+    int rc = dalloc(h, &h->adj3, (size_t)h->B * 3 * std::max(h->Mg(), h->Np()), "adjoint meshes");
+    if (rc) return rc;
+    return dalloc(h, &h->d_dot, (size_t)h->B, "adjoint dot");
+}
+}  // namespace
+
+int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adisp, float* avel, int32_t step_end) {
+    if (!h) return PM_ERR_ARG;
+    if (!disp || !vel || !adisp || !avel) return h->fail(PM_ERR_ARG, "pm_adjoint: NULL buffer");
+    if (h->ngrids != 1) return h->fail(PM_ERR_UNSUPPORTED, "pm_adjoint: interlaced grids are not supported");
+    if (step_end < 0 || step_end > (int)h->table.size())
+        return h->fail(PM_ERR_ARG, "pm_adjoint: step_end %d out of [0, %d]", step_end, (int)h->table.size());
+    int rc;
+    if ((rc = adj_alloc(h))) return rc;
+    cudaStream_t st = h->stream;
+    const int n = h->ng, l2 = ilog2i(n), order = h->cfg.order;
+    const long long Mg = h->Mg(), S = spec_elems(n);
+    const PmGeom gd = geom(h, n, h->rho_slot());
+    const PmGeom g3 = geom(h, n, 3 * Mg);
+    for (int s = step_end - 1; s >= 0; --s) {
+        const SlotCoef* coef = h->d_table + s;
+        cudaMemsetAsync(h->rho, 0, sizeof(float) * h->rho_slot() * h->B, st);
+        h->phase(0, 1);
+        pm_adj_drift_deposit(order, gd, disp, vel, adisp, avel, coef, 0, h->rho, h->B, st);
+        h->phase_end();
+        if ((rc = spectral_force(h, h->rho, h->rho_slot(), Mg, (float)(1.0 / (double)h->Np()), h->force, h->B)))
+            return rc;
+        cudaMemsetAsync(h->adj3, 0, sizeof(float) * 3 * Mg * h->B, st);
+        h->phase(6, 1);
+        pm_adj_interp(order, g3, disp, vel, adisp, avel, coef, 0, h->force, h->adj3, h->B, st);
+        h->phase_end();
+        // rho* = sum_c G_c^T s_c, G_c^T = (1/N) IDFT diag(conj m_c) DFT
+        h->phase(9, 5);
+        pm_fft_r2c_x(l2, h->adj3, Mg, h->spec, S, 3 * h->B, h->d_tw[l2], st);
+        pm_fft_y(l2, h->spec, S, 3 * h->B, -1, h->d_tw[l2], st);
+        PmZPass z{};
+        for (int c = 0; c < 3; ++c) z.in[c] = h->spec + c * S;
+        z.out[0] = h->spec;
+        z.slot_stride = 3 * S;
+        z.tw = h->d_tw[l2];
+        z.lap1 = h->d_lap;
+        z.grad1 = h->d_grad;
+        z.scale = (float)(1.0 / (double)h->Np());
+        pm_fft_z(l2, PM_Z_ADJ, z, h->B, st);
+        pm_fft_y(l2, h->spec, 3 * S, h->B, 1, h->d_tw[l2], st);
+        pm_fft_c2r_x(l2, h->spec, 3 * S, h->rho, h->rho_slot(), nullptr, 0, 0.f, h->B, h->d_tw[l2], st);
+        h->phase_end();
+        h->phase(6, 1);
+        pm_adj_gather_grad(order, 1, gd, disp, vel, adisp, avel, coef, 0, h->rho, 0.f, h->B, st);
+        h->phase_end();
+        if ((rc = h->check_launch("pm_adjoint step"))) return rc;
+    }
+    return PM_OK;
+}
+
+int pm_ic_adjoint(pm_handle* h, const float* noise, const float* adisp, const float* avel, float* anoise,
+                  double* dsigma8) {
+    if (!h) return PM_ERR_ARG;
+    if (!noise || !adisp || !avel || !anoise) return h->fail(PM_ERR_ARG, "pm_ic_adjoint: NULL buffer");
+    int rc;
+    if ((rc = adj_alloc(h))) return rc;
+    cudaStream_t st = h->stream;
+    const int n = h->np, l2 = ilog2i(n);
+    const long long Np = h->Np(), S = spec_elems(n);
+    // psi1* = D(a_ini) X*0 + V*0  (Psi0 = D psi1, V0 = psi1)
+    const float Dini = (float)h->growth->D(h->cfg.a_ini);
+    pm_axpby(h->adj3, adisp, avel, Dini, 1.f, 3 * Np * h->B, st);
+    // w* = sum_c F_IC,c^T psi1*_c
+    pm_fft_r2c_x(l2, h->adj3, Np, h->spec, S, 3 * h->B, h->d_tw[l2], st);
+    pm_fft_y(l2, h->spec, S, 3 * h->B, -1, h->d_tw[l2], st);
+    PmZPass z{};
+    for (int c = 0; c < 3; ++c) z.in[c] = h->spec + c * S;
+    z.out[0] = h->spec;
+    z.slot_stride = 3 * S;
+    z.tw = h->d_tw[l2];
+    z.ictab = h->d_ictab;
+    z.kf = (float)(2.0 * M_PI / h->cfg.box);
+    pm_fft_z(l2, PM_Z_IC_ADJ, z, h->B, st);
+    pm_fft_y(l2, h->spec, 3 * S, h->B, 1, h->d_tw[l2], st);
+    pm_fft_c2r_x(l2, h->spec, 3 * S, anoise, Np, nullptr, 0, 0.f, h->B, h->d_tw[l2], st);
+    if ((rc = h->check_launch("pm_ic_adjoint"))) return rc;
+    if (dsigma8) {
+        // psi1 is linear in the noise and proportional to sigma8: dL/dsigma8 = <w*, w> / sigma8
+        cudaMemsetAsync(h->d_dot, 0, sizeof(double) * h->B, st);
+        pm_dot(anoise, noise, Np, h->d_dot, h->B, st);
+        std::vector<double> d(h->B);
+        if (cudaMemcpyAsync(d.data(), h->d_dot, sizeof(double) * h->B, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return h->fail(PM_ERR_CUDA, "pm_ic_adjoint: readback");
+        for (int b = 0; b < h->B; ++b) dsigma8[b] = d[b] / h->cfg.sigma8;
+    }
+    return h->check_launch("pm_ic_adjoint");
+}
+
+int pm_density_vjp(pm_handle* h, const float* disp, int32_t n, int32_t order, const float* ddelta, float* adisp) {
+    if (!h) return PM_ERR_ARG;
+    if (!disp || !ddelta || !adisp) return h->fail(PM_ERR_ARG, "pm_density_vjp: NULL buffer");
+    if (!pow2_in_range(n)) return h->fail(PM_ERR_ARG, "mesh %d must be a power of two in [16, 1024]", n);
+    if (order != 2 && order != 3) return h->fail(PM_ERR_ARG, "order must be 2 or 3");
+    const long long M = mesh_elems(n);
+    // delta = (M/N) sum_i W(r_j - X_i) - 1  =>  X*_i = (M/N) sum_j delta*_j d/dX_i W(r_j - X_i)
+    pm_adj_gather_grad(order, 0, geom(h, n, M), const_cast<float*>(disp), nullptr, adisp, nullptr, nullptr, 0, ddelta,
+                       (float)((double)M / (double)h->Np()), h->B, h->stream);
+    return h->check_launch("pm_density_vjp");
 }
 
 int pm_profile(pm_handle* h, int32_t enable) {

@@ -20,7 +20,7 @@ struct PmZPass {
     float kf;
 };
 
-enum { PM_Z_FORCE = 0, PM_Z_FORCE_IL = 1, PM_Z_IC = 2, PM_Z_PK = 3, PM_Z_ADJ = 4 };
+enum { PM_Z_FORCE = 0, PM_Z_FORCE_IL = 1, PM_Z_IC = 2, PM_Z_PK = 3, PM_Z_ADJ = 4, PM_Z_IC_ADJ = 5 };
 
 int pm_fft_r2c_x(int log2n, const float* in, long long in_stride, float2* out, long long out_stride, int nmesh,
                  const float2* tw, cudaStream_t st);
@@ -48,3 +48,14 @@ int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float
 // acc[b][c][i] = sum_j g_c,j W(r_j - X_i) at X = q + disp (no kick): stage-level interpolation.
 int pm_interp(int order, int interlace, const PmGeom& g, const float* disp, const float* force, float* acc,
               int nslots, cudaStream_t st);
+
+// Adjoint (Sec. 2.7, Table 5; App. C pullbacks).  See particles.cu.
+int pm_adj_drift_deposit(int order, const PmGeom& g, float* disp, const float* vel, const float* adisp, float* avel,
+                         const SlotCoef* coef, int cstride, float* rho, int nslots, cudaStream_t st);
+int pm_adj_interp(int order, const PmGeom& g, const float* disp, float* vel, float* adisp, const float* avel,
+                  const SlotCoef* coef, int cstride, const float* force, float* s3, int nslots, cudaStream_t st);
+int pm_adj_gather_grad(int order, int finish, const PmGeom& g, float* disp, const float* vel, float* adisp,
+                       float* avel, const SlotCoef* coef, int cstride, const float* rhoa, float scale, int nslots,
+                       cudaStream_t st);
+int pm_dot(const float* a, const float* b, long long n, double* out, int nslots, cudaStream_t st);
+int pm_axpby(float* out, const float* x, const float* y, float a, float b, long long n, cudaStream_t st);

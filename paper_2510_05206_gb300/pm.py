@@ -184,8 +184,34 @@ class PM:
         self._check(self.lib.pm_interp(self.h, _ptr(disp), _ptr(force), _ptr(out)))
         return out
 
+    def adjoint(self, disp, vel, adj_disp, adj_vel, step_end=None):
+        """Backward DKD in place: (disp, vel) -> initial state, (adj_disp, adj_vel) -> initial cotangents."""
+        for t, nm in ((disp, "disp"), (vel, "vel"), (adj_disp, "adj_disp"), (adj_vel, "adj_vel")):
+            self._state_ok(t, nm, (self.B, 3, self.N))
+        self._stream()
+        end = self.cfg.n_steps if step_end is None else step_end
+        self._check(self.lib.pm_adjoint(self.h, _ptr(disp), _ptr(vel), _ptr(adj_disp), _ptr(adj_vel), int(end)))
+
+    def ic_adjoint(self, noise, adj_disp, adj_vel, with_sigma8=True):
+        out = torch.empty((self.B, self.N), device=self.device, dtype=torch.float32)
+        ds8 = np.zeros(self.B)
+        self._stream()
+        self._check(self.lib.pm_ic_adjoint(self.h, _ptr(noise), _ptr(adj_disp), _ptr(adj_vel), _ptr(out),
+                                           ds8.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if with_sigma8
+                                           else None))
+        return out, (ds8 if with_sigma8 else None)
+
+    def density_vjp(self, disp, ddelta, n_mesh=None, order=None):
+        n = n_mesh or self.cfg.n_mesh
+        self._state_ok(ddelta, "dL_ddelta", (self.B, n, n, n))
+        out = torch.empty((self.B, 3, self.N), device=self.device, dtype=torch.float32)
+        self._stream()
+        self._check(self.lib.pm_density_vjp(self.h, _ptr(disp), int(n), int(order or self.cfg.order), _ptr(ddelta),
+                                            _ptr(out)))
+        return out
+
     PHASES = ("deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv",
-              "interp_kick_drift", "ic_zeldovich", "power_spectrum", "reserved")
+              "interp_kick_drift", "ic_zeldovich", "power_spectrum", "adjoint_spectral")
 
     def profile(self, enable=True):
         self._check(self.lib.pm_profile(self.h, int(bool(enable))))

@@ -1,0 +1,151 @@
+"""GPU reverse mode (Sec. 2.7 adjoint method, Table 5; App. C scatter/gather
+VJPs) through the C ABI, against the FP64 oracle's adjoint, central finite
+differences of the GPU forward model, reversibility and step-count-independent
+memory.
+
+Loss (the field-level chi^2 of the adjoint workload): L = 1/2 sum_j ((delta_j - d_j)/sigma)^2
+with delta the final CIC/TSC density contrast on the PM mesh.
+
+Tolerances: the oracle comparison uses max |g_gpu - g_oracle| / max |g_oracle|:
+2e-4 with TSC (smooth kernel; float32 errors of the backward reintegration
+~1e-6 relative are amplified by the force Jacobian), and a relative L2 error of
+2e-3 with CIC (a float32 position that lands on the other side of a cell face
+changes a CIC derivative by O(1) for that particle, so isolated entries differ).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mesh, nbody
+from paper_2510_05206_gb300 import PM, Config, autodiff, inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=DEV)
+
+
+def _cfgs(n, n_mesh, L, order, steps, sigma8=0.8):
+    g = Config(n_part=n, n_mesh=n_mesh, box=L, order=order, n_steps=steps, sigma8=sigma8)
+    o = nbody.Config(n_part=n, n_mesh=n_mesh, box=L, order=order, n_steps=steps, sigma8=sigma8)
+    return g, o
+
+
+def _gpu_grad(pm, w, target, sigma):
+    noise = _t(w.reshape(1, -1)).requires_grad_(True)
+    disp, vel = autodiff.simulate(pm, noise)
+    delta = autodiff.density(pm, disp)
+    loss = 0.5 * (((delta.double() - target) / sigma) ** 2).sum()
+    loss.backward()
+    return float(loss.detach()), noise.grad[0].double().cpu().numpy().reshape(w.shape)
+
+
+def _oracle_grad(ocfg, w, target, sigma):
+    P0, V0 = nbody.zeldovich_ic(ocfg, w)
+    P, V = nbody.run(ocfg, P0, V0)
+    X = np.mod(nbody.lattice(ocfg.n_part, ocfg.box) + P, ocfg.box)
+    delta = mesh.density_contrast(X, ocfg.n_mesh, ocfg.box, ocfg.order)
+    Xa = nbody.density_vjp(ocfg, P, (delta - target) / sigma ** 2)
+    _, _, Xa0, Va0 = nbody.adjoint(ocfg, P, V, Xa, np.zeros_like(V))
+    wa, ds8 = nbody.ic_vjp(ocfg, Xa0, Va0, w)
+    return wa, ds8
+
+
+@pytest.mark.parametrize("order", [3, 2])
+def test_adjoint_gradient_matches_oracle(order):
+    n, L, sigma = 32, 200.0, 0.1
+    cfg, ocfg = _cfgs(n, n, L, order, 4)
+    pm = PM(cfg, device=DEV)
+    w = inputs.white_noise(n, seed=31)
+    target = 0.5 * inputs.white_noise(n, seed=32)
+    _, g = _gpu_grad(pm, w, _t(target[None]).double(), sigma)
+    ref, _ = _oracle_grad(ocfg, w, target, sigma)
+    if order == 3:
+        assert np.max(np.abs(g - ref)) / np.max(np.abs(ref)) < 2e-4
+    else:
+        assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 2e-3
+
+
+def test_sigma8_gradient_matches_oracle():
+    n, L, sigma = 32, 200.0, 0.1
+    cfg, ocfg = _cfgs(n, n, L, 3, 3)
+    pm = PM(cfg, device=DEV)
+    w = inputs.white_noise(n, seed=33)
+    target = 0.5 * inputs.white_noise(n, seed=34)
+    disp, vel = pm.ic_zeldovich(_t(w.reshape(1, -1)))
+    pm.run(disp, vel)
+    delta = pm.density(disp)
+    ddelta = ((delta.double() - _t(target[None]).double()) / sigma ** 2).float().contiguous()
+    ad = pm.density_vjp(disp, ddelta)
+    av = torch.zeros_like(ad)
+    pm.adjoint(disp, vel, ad, av)
+    _, ds8 = pm.ic_adjoint(_t(w.reshape(1, -1)), ad, av)
+    _, ref = _oracle_grad(ocfg, w, target, sigma)
+    assert ds8[0] == pytest.approx(ref, rel=2e-4)
+
+
+def test_adjoint_reintegrates_initial_state():
+    n, L = 32, 256.0
+    pm = PM(Config(n_part=n, n_mesh=n, box=L, n_steps=6), device=DEV)
+    noise = _t(inputs.white_noise(n, seed=35).reshape(1, -1))
+    d0, v0 = pm.ic_zeldovich(noise)
+    d, v = d0.clone(), v0.clone()
+    pm.run(d, v)
+    ad, av = torch.zeros_like(d), torch.zeros_like(v)
+    pm.adjoint(d, v, ad, av)
+    # float32: a rounding error e ~ 1e-7 |Psi(a=1)| excites the decaying mode,
+    # which grows backwards in time by ~ (D(1)/D(a_ini))^{3/2} ~ 240 here, while
+    # |Psi(a=1)| ~ 40 |Psi(a_ini)|: expect max errors ~1e-3 of rms |Psi(a_ini)|
+    # (the FP64 oracle reintegrates to 1e-10, tests/test_oracle_nbody.py).
+    rms = torch.sqrt((d0 ** 2).sum(1).mean())
+    assert float((d - d0).abs().max() / rms) < 2e-3
+    assert float(torch.sqrt(((d - d0) ** 2).sum(1).mean()) / rms) < 2e-4
+    assert float((v - v0).abs().max() / torch.sqrt((v0 ** 2).sum(1).mean())) < 2e-3
+    assert float(ad.abs().max()) == 0.0 and float(av.abs().max()) == 0.0
+
+
+def test_adjoint_vs_central_differences_gpu():
+    # directional derivatives of the float32 GPU forward model vs the adjoint
+    n, L, sigma = 32, 200.0, 0.1
+    cfg, _ = _cfgs(n, n, L, 3, 4)
+    pm = PM(cfg, device=DEV)
+    w = inputs.white_noise(n, seed=36)
+    target = _t(0.5 * inputs.white_noise(n, seed=37)[None]).double()
+    _, g = _gpu_grad(pm, w, target, sigma)
+    rng = np.random.default_rng(38)
+
+    def loss(wv):
+        disp, vel = pm.ic_zeldovich(_t(wv.reshape(1, -1)))
+        pm.run(disp, vel)
+        return float(0.5 * (((pm.density(disp).double() - target) / sigma) ** 2).sum())
+
+    errs = []
+    for _ in range(8):
+        e = rng.normal(size=w.shape)
+        e /= np.linalg.norm(e)
+        eps = 1e-2 * np.linalg.norm(w)
+        fd = (loss(w + eps * e) - loss(w - eps * e)) / (2 * eps)
+        errs.append(abs(np.sum(g * e) - fd) / abs(fd))
+    assert np.median(errs) < 2e-2, errs
+
+
+def test_adjoint_memory_independent_of_steps():
+    n, L = 64, 256.0
+    used = []
+    for steps in (2, 8):
+        pm = PM(Config(n_part=n, n_mesh=n, box=L, n_steps=steps), device=DEV)
+        noise = _t(inputs.white_noise(n, seed=39).reshape(1, -1))
+        d, v = pm.ic_zeldovich(noise)
+        pm.run(d, v)
+        ad, av = torch.ones_like(d), torch.zeros_like(v)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        pm.adjoint(d, v, ad, av)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        used.append(free0 - free1)
+        pm.close()
+    # the first adjoint call allocates its scratch once; identical for 2 and 8 steps
+    assert used[0] == used[1]
