@@ -404,7 +404,8 @@ int pm_init(const pm_config* cfg, void* stream, pm_handle** out) {
     if ((rc = dalloc(h.get(), &h->d_table, (size_t)cfg->n_steps, "step table"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->d_slots, (size_t)B, "slot table"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->d_unit, 1, "unit coef"))) return bail(rc);
-    for (int n : {h->ng, h->np, h->npk})
+    // twiddles for every size a call may use (P(k) and density meshes may be smaller than n_mesh)
+    for (int n = 16; n <= h->nmax; n *= 2)
         if ((rc = upload_twiddles(h.get(), n))) return bail(rc);
     // the padding columns of the spectra are transformed by the column passes: keep them finite
     if (cudaMemset(h->spec, 0, sizeof(float2) * B * h->spec_slot()) != cudaSuccess) {

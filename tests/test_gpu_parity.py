@@ -144,6 +144,19 @@ def test_power_spectrum_stage():
     assert np.max(np.abs(pk[0][ok] / pr[ok] - 1)) < 1e-4
 
 
+def test_power_spectrum_on_smaller_mesh_than_handle():
+    # P(k) meshes below n_mesh use their own twiddle tables (regression test)
+    n_part, L = 64, 300.0
+    pm = PM(Config(n_part=n_part, n_mesh=64, box=L), device=DEV)
+    Psi = inputs.random_displacements(n_part, scale=5.0, seed=6)
+    X = np.mod(nbody.lattice(n_part, L) + Psi, L)
+    for n, nb in ((32, 12), (16, 8), (64, 32)):
+        k, pk, cnt = pm.power_spectrum(_t(Psi[None]), n, nb)
+        kr, pr, cr = mesh.power_spectrum(mesh.density_contrast(X, n, L, 2), L, nb)
+        np.testing.assert_array_equal(cnt[0], cr)
+        assert np.max(np.abs(pk[0] / pr - 1)) < 1e-4
+
+
 def test_batched_slots_match_single_runs():
     n, L = 32, 256.0
     B = 3
