@@ -198,6 +198,30 @@ int pm_profile_read(pm_handle* h, double* ms, int64_t* calls, int64_t* launches,
  * first call (owned by the handle).  Synchronises the stream. */
 int pm_simulate_host(pm_handle* h, const float* noise, float* disp, float* vel);
 
+/* Largest mesh pm_power_spectrum_static accepts (cells per dimension). */
+#define PM_STATIC_PK_MAX_MESH 64
+
+/* Power spectrum for callers that cannot allocate device memory (host
+ * callbacks or pipelines that forbid cudaMalloc, plugins whose host owns every
+ * allocation, processes whose device budget is already committed).  The paper
+ * has no counterpart: it is the estimator of pm_power_spectrum (same bins and
+ * normalisation, CIC, one simulation) without a handle.
+ * disp: device [3][n_part^3] displacements (the particle layout above),
+ * n_part a power of two in [16, 1024], box > 0, n_mesh a power of two in
+ * [16, PM_STATIC_PK_MAX_MESH], n_bins in [1, n_mesh/2]; stream: cudaStream_t
+ * (NULL = legacy default stream); k, pk, n_modes: HOST arrays of n_bins.
+ * Allocates nothing: its ~2.4 MB of scratch is one file-scope __device__ array
+ * that every GPU which loads libpmgb holds until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call reuses the same array and clears what must start at zero, so calls
+ * that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Synchronises the stream.  Returns PM_ERR_ARG for
+ * sizes outside the limits (use the handle API for larger meshes) and
+ * PM_ERR_CUDA if a CUDA call fails. */
+int pm_power_spectrum_static(const float* disp, int32_t n_part, double box, int32_t n_mesh, int32_t n_bins,
+                             void* stream, double* k, double* pk, int64_t* n_modes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,8 @@ _SIGS = {
     "pm_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
     "pm_ic_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
     "pm_density_vjp": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
+    "pm_power_spectrum_static": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_int32, c_void_p,
+                                           POINTER(c_double), POINTER(c_double), POINTER(c_int64)]),
     "pm_profile": (c_int32, [c_void_p, c_int32]),
     "pm_profile_read": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), POINTER(c_int64), c_int32]),
     "pm_simulate_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),

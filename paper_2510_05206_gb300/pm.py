@@ -236,3 +236,20 @@ class PM:
         self._check(self.lib.pm_simulate_host(self.h, ctypes.c_void_p(noise.data_ptr()),
                                               ctypes.c_void_p(disp.data_ptr()), ctypes.c_void_p(vel.data_ptr())))
         return disp, vel
+
+
+def power_spectrum_static(disp, n_part, box, n_mesh, n_bins, stream=None):
+    """pm_power_spectrum_static: P(k) of one simulation without any device
+    allocation (fixed scratch inside the library, n_mesh <= 64)."""
+    lib = _lib.load()
+    k = np.zeros(n_bins)
+    pk = np.zeros(n_bins)
+    cnt = np.zeros(n_bins, dtype=np.int64)
+    s = stream if stream is not None else torch.cuda.current_stream(disp.device).cuda_stream
+    rc = lib.pm_power_spectrum_static(ctypes.c_void_p(disp.data_ptr()), int(n_part), float(box), int(n_mesh),
+                                      int(n_bins), ctypes.c_void_p(s),
+                                      k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      pk.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    _lib.check(rc)
+    return k, pk, cnt
