@@ -128,4 +128,101 @@ __device__ __forceinline__ void fft_lines(float2* s, const float2* tw, int twstr
     if constexpr (REM == 2) stage<N, 2, NSR, NL, LS, ES, DIR>(s, tw, twstride, active);
 }
 
+
+// ---------------------------------------------------------------------------
+// Functor form: the first stage reads its inputs through `ld(line, e)` and the
+// last stage writes through `st(line, e, v)`, so a transform can start from
+// global memory (or another tile, with an elementwise multiplier applied on the
+// fly) and end in global memory without an extra shared-memory round trip.
+// Middle stages work in place on the shared-memory tile `sm`.
+
+template <int N, int R, int NS, int NL, int DIR, bool MIDSYNC, class Ld, class St>
+__device__ __forceinline__ void stage_io(const Ld& ld, const St& st, const float2* tw, int twstride, bool active) {
+    constexpr int NB = 8 / R;
+    const int line = threadIdx.x % NL;
+    const int j = threadIdx.x / NL;
+    float2 v[8];
+    if (active) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int jj = j + b * (N / 8);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b * R + r] = ld(line, jj + r * (N / R));
+        }
+    }
+    if (MIDSYNC) __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int jj = j + b * (N / 8);
+            const int k = jj % NS;
+            float2* vb = v + b * R;
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) vb[r] = cmul(vb[r], twiddle<DIR>(tw, (r * k * (N / (NS * R))) * twstride));
+            }
+            if (R == 8) dft8<DIR>(vb);
+            if (R == 4) dft4<DIR>(vb[0], vb[1], vb[2], vb[3]);
+            if (R == 2) dft2<DIR>(vb[0], vb[1]);
+            const int o = (jj / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) st(line, o + r * NS, vb[r]);
+        }
+    }
+}
+
+// radix of stage i (0-based) and Ns before it for an N-point transform
+template <int N>
+struct Plan {
+    static constexpr int L2 = ilog2(N);
+    static constexpr int N8 = L2 / 3;
+    static constexpr int REM = 1 << (L2 - 3 * N8);
+    static constexpr int S = N8 + (REM > 1 ? 1 : 0);
+    __host__ __device__ static constexpr int radix(int i) { return i < N8 ? 8 : REM; }
+    __host__ __device__ static constexpr int ns(int i) { return 1 << (3 * (i < N8 ? i : N8)); }
+};
+
+// Full transform: ld -> (stage 0) -> sm -> ... -> (last stage) -> st.
+// FIRST_SYNC: stage 0 reads from `sm` itself (in-place first stage).
+// LAST_SMEM:  st writes into `sm` (in-place last stage).
+// The caller guarantees `sm` may be overwritten on entry (barrier before) and
+// synchronises after if st wrote shared memory that others read.
+template <int N, int NL, int DIR, bool FIRST_SYNC, bool LAST_SMEM, class Ld, class St, class Sm>
+__device__ __forceinline__ void fft_io(const Ld& ld, const St& st, const Sm& sm, const float2* tw, int twstride) {
+    using Pl = Plan<N>;
+    static_assert(Pl::S >= 2, "N must have at least two stages");
+    const bool active = threadIdx.x < NL * N / 8;
+    stage_io<N, Pl::radix(0), 1, NL, DIR, FIRST_SYNC>(ld, sm, tw, twstride, active);
+    __syncthreads();
+    if constexpr (Pl::S > 2) {
+        stage_io<N, Pl::radix(1), Pl::ns(1), NL, DIR, true>(sm, sm, tw, twstride, active);
+        __syncthreads();
+    }
+    if constexpr (Pl::S > 3) {
+        stage_io<N, Pl::radix(2), Pl::ns(2), NL, DIR, true>(sm, sm, tw, twstride, active);
+        __syncthreads();
+    }
+    static_assert(Pl::S <= 4, "at most 4 stages (N <= 4096)");
+    stage_io<N, Pl::radix(Pl::S - 1), Pl::ns(Pl::S - 1), NL, DIR, LAST_SMEM>(sm, st, tw, twstride, active);
+}
+
+// Shared-memory column tile of NL = COL_TILE columns: element e of column l at
+// (e + e / 8) * NL + l (one padding row every 8 rows keeps the radix-8 first
+// stage's stores free of bank conflicts).
+struct ColTile {
+    float2* s;
+    __device__ __forceinline__ int at(int l, int e) const { return (e + (e >> 3)) * COL_TILE + l; }
+    __device__ __forceinline__ float2 operator()(int l, int e) const { return s[at(l, e)]; }
+    __device__ __forceinline__ void operator()(int l, int e, float2 v) const { s[at(l, e)] = v; }
+};
+__host__ __device__ constexpr int col_tile_elems(int n) { return (n + n / 8) * COL_TILE; }
+
+// Global column tile: element e of column l at g[e * es + l]
+struct GCols {
+    float2* g;
+    long long es;
+    __device__ __forceinline__ float2 operator()(int l, int e) const { return g[e * es + l]; }
+    __device__ __forceinline__ void operator()(int l, int e, float2 v) const { g[e * es + l] = v; }
+};
+
 }  // namespace pmfft

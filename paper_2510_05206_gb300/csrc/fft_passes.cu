@@ -103,45 +103,78 @@ __global__ void __launch_bounds__(256) k_fft_x_c2r(const float2* __restrict__ in
     }
 }
 
-// ---------------------------------------------------------------- column tiles
-// A tile is COL_TILE adjacent kx columns of one (z) plane (y pass) or one (y) row
-// (z pass), all n elements along the transform axis; element e of column l
-// sits at tile[e * COL_TILE + l].
-template <int n>
-__device__ __forceinline__ void load_cols(float2* tile, const float2* __restrict__ base, long long estride) {
-    constexpr int Q = COL_TILE / 2;   // float4 per element row
-    for (int i = threadIdx.x; i < n * Q; i += blockDim.x) {
-        const int e = i / Q, c = i % Q;
-        const float4 v = reinterpret_cast<const float4*>(base + e * estride)[c];
-        tile[e * COL_TILE + 2 * c] = make_float2(v.x, v.y);
-        tile[e * COL_TILE + 2 * c + 1] = make_float2(v.z, v.w);
+
+// ---------------------------------------------------------------- x pass, C2R x3 -> float4
+// The three force spectra of one slot and grid, inverse transformed together and
+// written interleaved as one float4 mesh (gx, gy, gz, 0): the interpolation then
+// gathers one 16-byte value per tap.
+template <int LOG2N>
+__global__ void __launch_bounds__(768) k_fft_x_c2r3(const float2* __restrict__ in, long long comp_stride,
+                                                    long long slot_stride, float4* __restrict__ out,
+                                                    long long out_stride, const float2* __restrict__ twg) {
+    constexpr int n = 1 << LOG2N, N = n / 2, P = N + SPEC_PAD;
+    constexpr int ROWS = (2048 / N) < n * n ? (2048 / N) : n * n;
+    constexpr int LS = N + 1;
+    constexpr int L = 3 * ROWS;                         // lines: component-major, then row
+    extern __shared__ float2 sm[];
+    float2* tile = sm;
+    float2* tw = sm + L * LS;
+    const int q = blockIdx.y;
+    const long long row0 = (long long)blockIdx.x * ROWS;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    for (int i = threadIdx.x; i < L * (N + 1); i += blockDim.x) {
+        const int line = i / (N + 1), k = i % (N + 1);
+        const int c = line / ROWS, r = line % ROWS;
+        tile[line * LS + k] = in[q * slot_stride + c * comp_stride + (row0 + r) * P + k];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < L * (N / 2 + 1); i += blockDim.x) {
+        const int line = i / (N / 2 + 1), k = i % (N / 2 + 1);
+        float2* t = tile + line * LS;
+        const float2 a = t[k], b = t[N - k];
+        const float2 ek = cadd(a, cconj(b));
+        const float2 ok = cmul(csub(a, cconj(b)), cconj(tw[k]));
+        const float2 zk = cadd(ek, cmul_i(ok, 1));
+        if (k > 0 && k < N / 2) {
+            const float2 em = cadd(b, cconj(a));
+            const float2 om = cmul(csub(b, cconj(a)), cconj(tw[N - k]));
+            t[N - k] = cadd(em, cmul_i(om, 1));
+        }
+        t[k] = zk;
+    }
+    __syncthreads();
+    fft_lines<N, L, LS, 1, 1>(tile, tw, 2);
+    float4* dst = out + q * out_stride + row0 * n;
+    for (int i = threadIdx.x; i < ROWS * n; i += blockDim.x) {
+        const int r = i / n, x = i % n;
+        const int m = x >> 1;
+        const float2 z0 = tile[(0 * ROWS + r) * LS + m];
+        const float2 z1 = tile[(1 * ROWS + r) * LS + m];
+        const float2 z2 = tile[(2 * ROWS + r) * LS + m];
+        dst[i] = (x & 1) ? make_float4(z0.y, z1.y, z2.y, 0.f) : make_float4(z0.x, z1.x, z2.x, 0.f);
     }
 }
 
-template <int n>
-__device__ __forceinline__ void store_cols(const float2* tile, float2* __restrict__ base, long long estride) {
-    constexpr int Q = COL_TILE / 2;
-    for (int i = threadIdx.x; i < n * Q; i += blockDim.x) {
-        const int e = i / Q, c = i % Q;
-        const float2 a = tile[e * COL_TILE + 2 * c], b = tile[e * COL_TILE + 2 * c + 1];
-        reinterpret_cast<float4*>(base + e * estride)[c] = make_float4(a.x, a.y, b.x, b.y);
-    }
-}
+// ---------------------------------------------------------------- column tiles
+// A column tile is COL_TILE adjacent kx columns of one z plane (y pass) or one
+// y row (z pass), all n elements along the transform axis.  The first FFT stage
+// reads it straight from global memory and the last stage writes it straight
+// back (fft_io), so a tile makes two shared-memory round trips per element for
+// n = 512 instead of four.
+__host__ __device__ constexpr int col_min_blocks(int log2n) { return (1024 >> log2n) > 32 ? 32 : ((1024 >> log2n) < 1 ? 1 : (1024 >> log2n)); }
 
 // y pass: grid (tiles, n planes, meshes)
 template <int LOG2N, int DIR>
-__global__ void __launch_bounds__(1 << LOG2N) k_fft_y(float2* __restrict__ data, long long stride,
-                                                      const float2* __restrict__ twg) {
+__global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_y(float2* __restrict__ data, long long stride,
+                                                                            const float2* __restrict__ twg) {
     constexpr int n = 1 << LOG2N, P = n / 2 + SPEC_PAD;
     extern __shared__ float2 sm[];
-    float2* tile = sm;
-    float2* tw = sm + n * COL_TILE;
+    float2* tw = sm;
+    const ColTile tile{sm + n};
     for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
-    float2* base = data + blockIdx.z * stride + (long long)blockIdx.y * n * P + blockIdx.x * COL_TILE;
-    load_cols<n>(tile, base, P);
-    __syncthreads();
-    fft_lines<n, COL_TILE, 1, COL_TILE, DIR>(tile, tw, 1);
-    store_cols<n>(tile, base, P);
+    const GCols g{data + blockIdx.z * stride + (long long)blockIdx.y * n * P + blockIdx.x * COL_TILE, P};
+    // the first stage needs no twiddles; the barrier after it publishes them
+    fft_io<n, COL_TILE, DIR, false, false>(g, g, tile, tw, 1);
 }
 
 // ---------------------------------------------------------------- z pass
@@ -163,92 +196,104 @@ struct ZArgs {
 enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5 };
 
 template <int LOG2N, int MODE>
-__global__ void __launch_bounds__(1 << LOG2N) k_fft_z(ZArgs a) {
+__global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZArgs a) {
     constexpr int n = 1 << LOG2N, P = n / 2 + SPEC_PAD;
-    constexpr int T = n * COL_TILE;
+    constexpr int TE = col_tile_elems(n);
     constexpr long long ES = (long long)n * P;      // z stride (complex)
     extern __shared__ float2 sm[];
-    float2* A = sm;                  // transformed input (forward along z)
-    float2* B = sm + T;              // work tile
-    float2* A2 = sm + 2 * T;         // second input (interlaced / adjoint)
-    float2* tw = sm + (MODE == Z_FORCE_IL || MODE == Z_ADJ || MODE == Z_IC_ADJ ? 3 : 2) * T;
-    float* lap = reinterpret_cast<float*>(tw + n);
+    float2* tw = sm;
+    float* lap = reinterpret_cast<float*>(sm + n);
     float* grad = lap + n;
+    const ColTile A{sm + 2 * n};
+    const ColTile B{sm + 2 * n + TE};
+    const ColTile A2{sm + 2 * n + 2 * TE};
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         tw[i] = a.tw[i];
-        if (MODE != Z_IC && MODE != Z_PK && MODE != Z_IC_ADJ) { lap[i] = a.lap1[i]; grad[i] = a.grad1[i]; }
+        if (MODE == Z_FORCE || MODE == Z_FORCE_IL || MODE == Z_ADJ) {
+            lap[i] = a.lap1[i];
+            grad[i] = a.grad1[i];
+        }
     }
     const int slot = blockIdx.z;
     const int y = blockIdx.y;
     const int kx0 = blockIdx.x * COL_TILE;
     const long long off = slot * a.slot_stride + (long long)y * P + kx0;
     const int my = freq_index(y, n);
+    const GCols in0{const_cast<float2*>(a.in[0]) + off, ES};
 
     if (MODE == Z_ADJ || MODE == Z_IC_ADJ) {
         // Z_ADJ: sum_c conj(m_c) x_c^, m_c = -i D1(k_c) / K_lap(k) * scale => conj(m_c) = +i D1 / K * scale
         // Z_IC_ADJ: sum_c conj(i k_c T(k^2)) x_c^ = -i T sum_c k_c x_c^ (every Nyquist plane zero)
-        load_cols<n>(A, a.in[0] + off, ES);
+        fft_io<n, COL_TILE, -1, false, true>(in0, A, A, tw, 1);
         __syncthreads();
-        fft_lines<n, COL_TILE, 1, COL_TILE, -1>(A, tw, 1);
-        for (int c = 1; c < 3; ++c) {
-            float2* X = c == 1 ? B : A2;
-            load_cols<n>(X, a.in[c] + off, ES);
-            __syncthreads();
-            fft_lines<n, COL_TILE, 1, COL_TILE, -1>(X, tw, 1);
-        }
-        for (int i = threadIdx.x; i < T; i += blockDim.x) {
-            const int e = i / COL_TILE, l = i % COL_TILE;
+        fft_io<n, COL_TILE, -1, false, true>(GCols{const_cast<float2*>(a.in[1]) + off, ES}, B, B, tw, 1);
+        __syncthreads();
+        fft_io<n, COL_TILE, -1, false, true>(GCols{const_cast<float2*>(a.in[2]) + off, ES}, A2, A2, tw, 1);
+        __syncthreads();
+        auto comb = [&](int l, int e) -> float2 {
             const int kx = kx0 + l;
             float2 r = make_float2(0.f, 0.f);
             if (MODE == Z_ADJ && kx <= n / 2 && (kx | y | e)) {
                 const float inv = a.scale / (lap[kx] + lap[y] + lap[e]);
-                // +i * (gx A + gy B + gz A2) * inv
-                const float2 s = cadd(cadd(cscale(A[i], grad[kx]), cscale(B[i], grad[y])), cscale(A2[i], grad[e]));
-                r = cmul_i(cscale(s, inv), 1);
+                const float2 s3 = cadd(cadd(cscale(A(l, e), grad[kx]), cscale(B(l, e), grad[y])), cscale(A2(l, e), grad[e]));
+                r = cmul_i(cscale(s3, inv), 1);
             }
             if (MODE == Z_IC_ADJ && kx < n / 2 && y != n / 2 && e != n / 2) {
                 const int mz = freq_index(e, n);
-                const int s2 = kx * kx + my * my + mz * mz;
-                const float f = a.kf * __ldg(&a.ictab[s2]);
-                const float2 s = cadd(cadd(cscale(A[i], (float)kx), cscale(B[i], (float)my)), cscale(A2[i], (float)mz));
-                r = cmul_i(cscale(s, f), -1);
+                const float f = a.kf * __ldg(&a.ictab[kx * kx + my * my + mz * mz]);
+                const float2 s3 = cadd(cadd(cscale(A(l, e), (float)kx), cscale(B(l, e), (float)my)), cscale(A2(l, e), (float)mz));
+                r = cmul_i(cscale(s3, f), -1);
             }
-            A[i] = r;
-        }
-        __syncthreads();
-        fft_lines<n, COL_TILE, 1, COL_TILE, 1>(A, tw, 1);
-        store_cols<n>(A, a.out[0] + off, ES);
+            return r;
+        };
+        fft_io<n, COL_TILE, 1, true, false>(comb, GCols{a.out[0] + off, ES}, A, tw, 1);
         return;
     }
 
-    load_cols<n>(A, a.in[0] + off, ES);
-    if (MODE == Z_FORCE_IL) load_cols<n>(A2, a.in[1] + off, ES);
+    fft_io<n, COL_TILE, -1, false, true>(in0, A, A, tw, 1);
+    if (MODE == Z_FORCE_IL) {
+        __syncthreads();
+        fft_io<n, COL_TILE, -1, false, true>(GCols{const_cast<float2*>(a.in[1]) + off, ES}, A2, A2, tw, 1);
+    }
     __syncthreads();
-    fft_lines<n, COL_TILE, 1, COL_TILE, -1>(A, tw, 1);
-    if (MODE == Z_FORCE_IL) fft_lines<n, COL_TILE, 1, COL_TILE, -1>(A2, tw, 1);
 
     if (MODE == Z_PK) {
-        // per-CTA FP64 bin sums in shared memory, then one global atomic per bin
-        double* acc = reinterpret_cast<double*>(B);     // 3 * nbins doubles (<= T float2)
-        for (int i = threadIdx.x; i < 3 * a.nbins; i += blockDim.x) acc[i] = 0.0;
+        // sum over the modes of each bin of w |delta^|^2 (w = 2 for 0 < kx < n/2, the
+        // half spectrum standing for +-kx), FP64: lanes of a warp that share a bin are
+        // reduced with shuffles, then one shared-memory atomic per bin and warp, then
+        // one global atomic per bin and CTA.  Mode counts and mean |k| per bin depend
+        // on the mesh only and are tabulated exactly on the host.
+        double* acc = reinterpret_cast<double*>(B.s);   // nbins doubles (<= TE float2)
+        for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) acc[i] = 0.0;
         __syncthreads();
-        for (int i = threadIdx.x; i < T; i += blockDim.x) {
+        const int lane = threadIdx.x & 31;
+        constexpr int T = n * COL_TILE;
+        for (int i = threadIdx.x; i < T; i += blockDim.x) {   // T is a multiple of blockDim: no divergence
             const int e = i / COL_TILE, l = i % COL_TILE;
             const int kx = kx0 + l;
-            if (kx > n / 2) continue;
-            const int mz = freq_index(e, n);
-            const int s = kx * kx + my * my + mz * mz;
-            const int b = a.bintab[s];
-            if (b < 0) continue;
-            const double w = (kx == 0 || kx == n / 2) ? 1.0 : 2.0;
-            const double re = A[i].x, im = A[i].y;
-            atomicAdd(&acc[b], w * (re * re + im * im));
-            atomicAdd(&acc[a.nbins + b], w * sqrt((double)s));
-            atomicAdd(&acc[2 * a.nbins + b], w);
+            int b = -1;
+            double v = 0.0;
+            if (kx <= n / 2) {
+                const int mz = freq_index(e, n);
+                b = a.bintab[kx * kx + my * my + mz * mz];
+                const float2 d = A(l, e);
+                v = ((kx == 0 || kx == n / 2) ? 1.0 : 2.0) * ((double)d.x * d.x + (double)d.y * d.y);
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
+            while (todo) {
+                const int leader = __ffs(todo) - 1;
+                const int bl = __shfl_sync(0xffffffffu, b, leader);
+                const bool mine = (b == bl);
+                double sv = mine ? v : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+                if (lane == leader) atomicAdd(&acc[bl], sv);
+                todo &= ~__ballot_sync(0xffffffffu, mine);
+            }
         }
         __syncthreads();
-        double* dst = a.pk_out + (long long)slot * 3 * a.nbins;
-        for (int i = threadIdx.x; i < 3 * a.nbins; i += blockDim.x)
+        double* dst = a.pk_out + (long long)slot * a.nbins;
+        for (int i = threadIdx.x; i < a.nbins; i += blockDim.x)
             if (acc[i] != 0.0) atomicAdd(&dst[i], acc[i]);
         return;
     }
@@ -256,45 +301,39 @@ __global__ void __launch_bounds__(1 << LOG2N) k_fft_z(ZArgs a) {
     const int ncomp = MODE == Z_FORCE_IL ? 6 : 3;
     for (int c = 0; c < ncomp; ++c) {
         const int axis = c % 3;
-        for (int i = threadIdx.x; i < T; i += blockDim.x) {
-            const int e = i / COL_TILE, l = i % COL_TILE;
+        auto mult = [&](int l, int e) -> float2 {
             const int kx = kx0 + l;
             float2 r = make_float2(0.f, 0.f);
-            if (kx <= n / 2) {
-                const int mz = freq_index(e, n);
-                if (MODE == Z_IC) {
-                    // psi1_c^ = i k_c T(k^2) w^, zero on every Nyquist plane
-                    if (kx != n / 2 && y != n / 2 && e != n / 2) {
-                        const int s = kx * kx + my * my + mz * mz;
-                        const int mc = axis == 0 ? kx : (axis == 1 ? my : mz);
-                        const float f = a.kf * (float)mc * __ldg(&a.ictab[s]);
-                        r = cmul_i(cscale(A[i], f), 1);
-                    }
-                } else {
-                    // g_c^ = -i D1(k_c) / K_lap(k) * scale * delta^   (k = 0 -> 0)
-                    const int bc = axis == 0 ? kx : (axis == 1 ? y : e);
-                    float2 d = A[i];
-                    bool keep = (kx | y | e) != 0;
-                    if (MODE == Z_FORCE_IL) {
-                        // delta^ = (d0^ + exp(i k.s) d1^) / 2, s = H/2 (1,1,1); every Nyquist plane zeroed
-                        keep = keep && kx != n / 2 && y != n / 2 && e != n / 2;
-                        const float ph = 3.14159265358979f / n * (float)(kx + my + mz);
-                        float sn, cs;
-                        sincosf(ph, &sn, &cs);
-                        d = cscale(cadd(d, cmul(make_float2(cs, sn), A2[i])), 0.5f);
-                        if (c >= 3) d = cmul(d, make_float2(cs, -sn));   // grid 1: g^ exp(-i k.s)
-                    }
-                    if (keep) {
-                        const float f = -grad[bc] * a.scale / (lap[kx] + lap[y] + lap[e]);
-                        r = cmul_i(cscale(d, f), 1);
-                    }
+            if (kx > n / 2) return r;
+            const int mz = freq_index(e, n);
+            if (MODE == Z_IC) {
+                // psi1_c^ = i k_c T(k^2) w^, zero on every Nyquist plane
+                if (kx != n / 2 && y != n / 2 && e != n / 2) {
+                    const int mc = axis == 0 ? kx : (axis == 1 ? my : mz);
+                    const float f = a.kf * (float)mc * __ldg(&a.ictab[kx * kx + my * my + mz * mz]);
+                    r = cmul_i(cscale(A(l, e), f), 1);
                 }
+                return r;
             }
-            B[i] = r;
-        }
-        __syncthreads();
-        fft_lines<n, COL_TILE, 1, COL_TILE, 1>(B, tw, 1);
-        store_cols<n>(B, a.out[c] + off, ES);
+            // g_c^ = -i D1(k_c) / K_lap(k) * scale * delta^   (k = 0 -> 0)
+            const int bc = axis == 0 ? kx : (axis == 1 ? y : e);
+            float2 d = A(l, e);
+            bool keep = (kx | y | e) != 0;
+            if (MODE == Z_FORCE_IL) {
+                // delta^ = (d0^ + exp(i k.s) d1^) / 2, s = H/2 (1,1,1); every Nyquist plane zeroed
+                keep = keep && kx != n / 2 && y != n / 2 && e != n / 2;
+                float sn, cs;
+                sincospif((float)(kx + my + mz) / n, &sn, &cs);
+                d = cscale(cadd(d, cmul(make_float2(cs, sn), A2(l, e))), 0.5f);
+                if (c >= 3) d = cmul(d, make_float2(cs, -sn));   // grid 1: g^ exp(-i k.s)
+            }
+            if (keep) {
+                const float f = -grad[bc] * a.scale / (lap[kx] + lap[y] + lap[e]);
+                r = cmul_i(cscale(d, f), 1);
+            }
+            return r;
+        };
+        fft_io<n, COL_TILE, 1, false, false>(mult, GCols{a.out[c] + off, ES}, B, tw, 1);
         __syncthreads();
     }
 }
@@ -338,9 +377,20 @@ void launch_x_c2r(const float2* in, long long in_stride, float* out, long long o
 }
 
 template <int LOG2N>
+void launch_x_c2r3(const float2* in, long long comp_stride, long long slot_stride, float4* out, long long out_stride,
+                   int nmesh, const float2* tw, cudaStream_t st) {
+    constexpr int n = 1 << LOG2N, N = n / 2;
+    const int rows = rows_per_cta<LOG2N>();
+    const size_t smem = (size_t)(3 * rows * (N + 1) + n) * sizeof(float2);
+    set_smem(k_fft_x_c2r3<LOG2N>, smem);
+    dim3 grid(n * n / rows, nmesh);
+    k_fft_x_c2r3<LOG2N><<<grid, 768, smem, st>>>(in, comp_stride, slot_stride, out, out_stride, tw);
+}
+
+template <int LOG2N>
 void launch_y(float2* data, long long stride, int nmesh, int dir, const float2* tw, cudaStream_t st) {
     constexpr int n = 1 << LOG2N;
-    const size_t smem = (size_t)(n * COL_TILE + n) * sizeof(float2);
+    const size_t smem = (size_t)(col_tile_elems(n) + n) * sizeof(float2);
     dim3 grid(n / 2 / COL_TILE + 1, n, nmesh);
     if (dir < 0) {
         set_smem(k_fft_y<LOG2N, -1>, smem);
@@ -355,7 +405,7 @@ template <int LOG2N, int MODE>
 void launch_z_mode(const ZArgs& a, int nslots, cudaStream_t st) {
     constexpr int n = 1 << LOG2N;
     const int ntile = (MODE == Z_FORCE_IL || MODE == Z_ADJ || MODE == Z_IC_ADJ) ? 3 : 2;
-    const size_t smem = (size_t)(ntile * n * COL_TILE + n) * sizeof(float2) + 2 * n * sizeof(float);
+    const size_t smem = (size_t)(ntile * col_tile_elems(n) + 2 * n) * sizeof(float2);
     dim3 grid(n / 2 / COL_TILE + 1, n, nslots);
     set_smem(k_fft_z<LOG2N, MODE>, smem);
     k_fft_z<LOG2N, MODE><<<grid, n, smem, st>>>(a);
@@ -397,6 +447,12 @@ int pm_fft_r2c_x(int log2n, const float* in, long long in_stride, float2* out, l
 int pm_fft_c2r_x(int log2n, const float2* in, long long in_stride, float* out, long long out_stride, float* out2,
                  long long out2_stride, float scale2, int nmesh, const float2* tw, cudaStream_t st) {
     PM_DISPATCH_LOG2N(log2n, (launch_x_c2r<LG>(in, in_stride, out, out_stride, out2, out2_stride, scale2, nmesh, tw, st)));
+    return 0;
+}
+
+int pm_fft_c2r_x3(int log2n, const float2* in, long long comp_stride, long long slot_stride, float4* out,
+                  long long out_stride, int nmesh, const float2* tw, cudaStream_t st) {
+    PM_DISPATCH_LOG2N(log2n, (launch_x_c2r3<LG>(in, comp_stride, slot_stride, out, out_stride, nmesh, tw, st)));
     return 0;
 }
 

@@ -108,6 +108,163 @@ __global__ void __launch_bounds__(256) k_deposit(PmGeom g, const float* __restri
     }
 }
 
+
+// Lagrangian-tile deposit through a shared-memory window.
+// A CTA owns a tile of (32/R) x (8/R) x (8/R) lattice sites (R = n_mesh / n_part in
+// {1, 2}), i.e. a 32 x 8 x 8 block of cells.  Pass 1 loads the tile's
+// drifted displacements (in cells) and their mean; the window is the tile's
+// cell block shifted by the rounded mean and padded by TILE_HALO cells.  Pass 2
+// adds each particle's ORDER^3 weights into the window with shared-memory
+// atomics (particles whose taps leave the window add straight to global
+// memory), and the window is flushed with 16-byte vector reductions, skipping
+// all-zero groups.  The x origin is aligned to 4 cells so that every group is
+// 16-byte aligned and never straddles the periodic boundary.
+// The window accumulates in unsigned fixed point, weight * 2^20 rounded: integer
+// shared-memory atomics are native (float ones are not), the sums are exact and
+// order-independent, and a cell cannot overflow since at most 2048 particles
+// (one tile) add at most 2^20 each.
+constexpr int TILE_HALO = 4;
+constexpr float DEP_FIX = 1048576.f;            // 2^20
+constexpr float DEP_UNFIX = 1.f / 1048576.f;
+
+template <int ORDER>
+struct DepWindow {
+    static constexpr int LO = ORDER == 3 ? 1 : 0;                           // taps below the base cell
+    static constexpr int WX = (32 + 2 * TILE_HALO + ORDER + 3 + 3) / 4 * 4;   // + alignment slack
+    static constexpr int WY = 8 + 2 * TILE_HALO + ORDER;
+    static constexpr int WZ = WY;
+    static constexpr int CELLS = WX * WY * WZ;
+};
+
+__device__ __forceinline__ void red_v4(float* p, float4 v) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+template <int ORDER, int R>
+__global__ void __launch_bounds__(256) k_deposit_tiled(PmGeom g, const float* __restrict__ disp,
+                                                       const float* __restrict__ vel,
+                                                       const SlotCoef* __restrict__ coef, int cstride, float shift,
+                                                       float* __restrict__ rho) {
+    using Win = DepWindow<ORDER>;
+    constexpr int TXP = 32 / R, TYP = 8 / R, TZP = 8 / R;
+    constexpr int PPT = TXP * TYP * TZP / 256;          // particles per thread
+    constexpr int RSTEP = 256 / TXP;                     // rows advanced per particle slot
+    extern __shared__ unsigned win[];
+    __shared__ float red[3][8];
+    const int slot = blockIdx.y;
+    const SlotCoef cf = coef[slot * cstride];
+    if (!cf.active) return;
+    const int np = 1 << g.log2np;
+    const int ntx = np / TXP, nty = np / TYP;
+    const int tile = blockIdx.x;
+    const int ix0 = (tile % ntx) * TXP;
+    const int iy0 = ((tile / ntx) % nty) * TYP;
+    const int iz0 = (tile / (ntx * nty)) * TZP;
+    const long long N = 1ll << (3 * g.log2np);
+    const float* d = disp + slot * g.slot_part;
+    const float* v = vel ? vel + slot * g.slot_part : nullptr;
+    const int t = threadIdx.x;
+    const int xp = t % TXP;
+
+    // pass 1: drifted displacements in cells, and the tile mean
+    float sx[PPT], sy[PPT], sz[PPT];
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int row = t / TXP + RSTEP * p;
+        const long long i = ((long long)(iz0 + row / TYP) * np + (iy0 + row % TYP)) * np + (ix0 + xp);
+        float a = d[i], b = d[N + i], c = d[2 * N + i];
+        if (v) {
+            a += cf.tau1 * v[i];
+            b += cf.tau1 * v[N + i];
+            c += cf.tau1 * v[2 * N + i];
+        }
+        sx[p] = a * g.inv_h + shift;
+        sy[p] = b * g.inv_h + shift;
+        sz[p] = c * g.inv_h + shift;
+        m0 += sx[p];
+        m1 += sy[p];
+        m2 += sz[p];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+        m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+        m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+    }
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = m0;
+        red[1][t >> 5] = m1;
+        red[2][t >> 5] = m2;
+    }
+    for (int i = t; i < Win::CELLS / 4; i += 256) reinterpret_cast<uint4*>(win)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    float mean[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += red[c][w];
+        mean[c] = sum * (1.f / (TXP * TYP * TZP));
+    }
+    const int ox = (ix0 * R + __float2int_rn(mean[0]) - TILE_HALO - Win::LO) & ~3;
+    const int oy = iy0 * R + __float2int_rn(mean[1]) - TILE_HALO - Win::LO;
+    const int oz = iz0 * R + __float2int_rn(mean[2]) - TILE_HALO - Win::LO;
+    const int ng = 1 << g.log2ng, msk = ng - 1;
+    float* m = rho + slot * g.slot_mesh;
+    const int ds = g.log2ng - g.log2np;
+
+    // pass 2: scatter into the window (or straight to global memory)
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int row = t / TXP + RSTEP * p;
+        const AxisTaps ax = axis_taps<ORDER>(ix0 + xp, ds, sx[p]);
+        const AxisTaps ay = axis_taps<ORDER>(iy0 + row % TYP, ds, sy[p]);
+        const AxisTaps az = axis_taps<ORDER>(iz0 + row / TYP, ds, sz[p]);
+        const int lx = ax.c - ox, ly = ay.c - oy, lz = az.c - oz;
+        const bool inside = lx >= 0 && lx + ORDER <= Win::WX && ly >= 0 && ly + ORDER <= Win::WY && lz >= 0 &&
+                            lz + ORDER <= Win::WZ;
+        if (inside) {
+#pragma unroll
+            for (int c = 0; c < ORDER; ++c)
+#pragma unroll
+                for (int b = 0; b < ORDER; ++b) {
+                    unsigned* wrow = win + ((lz + c) * Win::WY + (ly + b)) * Win::WX + lx;
+                    const float wzy = az.w[c] * ay.w[b] * DEP_FIX;
+#pragma unroll
+                    for (int a = 0; a < ORDER; ++a) atomicAdd(wrow + a, __float2uint_rn(wzy * ax.w[a]));
+                }
+        } else {
+#pragma unroll
+            for (int c = 0; c < ORDER; ++c) {
+                const long long zo = (long long)((az.c + c) & msk) * ng;
+#pragma unroll
+                for (int b = 0; b < ORDER; ++b) {
+                    const long long yo = (zo + ((ay.c + b) & msk)) * ng;
+                    const float wzy = az.w[c] * ay.w[b];
+#pragma unroll
+                    for (int a = 0; a < ORDER; ++a) atomicAdd(&m[yo + ((ax.c + a) & msk)], wzy * ax.w[a]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // flush: one 16-byte vector reduction per non-zero group of 4 cells
+    constexpr int QX = Win::WX / 4;
+    for (int i = t; i < Win::CELLS / 4; i += 256) {
+        const uint4 u = reinterpret_cast<const uint4*>(win)[i];
+        if ((u.x | u.y | u.z | u.w) == 0u) continue;
+        const float4 val = make_float4(u.x * DEP_UNFIX, u.y * DEP_UNFIX, u.z * DEP_UNFIX, u.w * DEP_UNFIX);
+        const int q = i % QX, yz = i / QX;
+        const int y = yz % Win::WY, z = yz / Win::WY;
+        const long long gi = ((long long)((oz + z) & msk) * ng + ((oy + y) & msk)) * ng + ((ox + 4 * q) & msk);
+        red_v4(m + gi, val);
+    }
+}
+
 // sum over taps of g_c at the particle, c = 0..2, meshes at f, f + M, f + 2M
 template <int ORDER>
 __device__ __forceinline__ void gather3(const float* __restrict__ f, long long M, int log2ng, const AxisTaps& ax,
@@ -129,6 +286,78 @@ __device__ __forceinline__ void gather3(const float* __restrict__ f, long long M
                 acc[2] += w * __ldg(&f[2 * M + j]);
             }
         }
+    }
+}
+
+// same from an interleaved float4 mesh (gx, gy, gz, 0): one 16-byte load per tap
+template <int ORDER>
+__device__ __forceinline__ void gather3v(const float4* __restrict__ f, int log2ng, const AxisTaps& ax,
+                                         const AxisTaps& ay, const AxisTaps& az, float acc[3]) {
+    const int ng = 1 << log2ng, msk = ng - 1;
+#pragma unroll
+    for (int c = 0; c < ORDER; ++c) {
+        const long long zo = (long long)((az.c + c) & msk) * ng;
+#pragma unroll
+        for (int b = 0; b < ORDER; ++b) {
+            const long long yo = (zo + ((ay.c + b) & msk)) * ng;
+            const float wzy = az.w[c] * ay.w[b];
+#pragma unroll
+            for (int a = 0; a < ORDER; ++a) {
+                const float4 v = __ldg(&f[yo + ((ax.c + a) & msk)]);
+                const float w = wzy * ax.w[a];
+                acc[0] += w * v.x;
+                acc[1] += w * v.y;
+                acc[2] += w * v.z;
+            }
+        }
+    }
+}
+
+// interpolation + kick + drift_2 from interleaved float4 force meshes [slot][grid][M]
+template <int ORDER, int IL>
+__global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict__ disp, float* __restrict__ vel,
+                                                     const SlotCoef* __restrict__ coef, int cstride,
+                                                     const float4* __restrict__ force4) {
+    const int slot = blockIdx.y;
+    const SlotCoef cf = coef[slot * cstride];
+    if (!cf.active) return;
+    const long long N = 1ll << (3 * g.log2np);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const Lattice L = lattice_index(i, g.log2np);
+    float* d = disp + slot * g.slot_part;
+    float* v = vel + slot * g.slot_part;
+    float p[3], u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        u[c] = v[c * N + i];
+        p[c] = d[c * N + i] + cf.tau1 * u[c];          // drift_1: X_half
+    }
+    const int ds = g.log2ng - g.log2np;
+    const long long M = 1ll << (3 * g.log2ng);
+    const float4* f = force4 + slot * g.slot_mesh;
+    float acc[3] = {0.f, 0.f, 0.f};
+    {
+        const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[0] * g.inv_h);
+        const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[1] * g.inv_h);
+        const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[2] * g.inv_h);
+        gather3v<ORDER>(f, g.log2ng, ax, ay, az, acc);
+    }
+    if (IL) {
+        // second grid shifted by half a cell; average the two interpolants
+        float acc1[3] = {0.f, 0.f, 0.f};
+        const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[0] * g.inv_h + 0.5f);
+        const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[1] * g.inv_h + 0.5f);
+        const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[2] * g.inv_h + 0.5f);
+        gather3v<ORDER>(f + M, g.log2ng, ax, ay, az, acc1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = 0.5f * (acc[c] + acc1[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float vn = cf.alpha * u[c] + cf.kick * acc[c];   // kick
+        v[c * N + i] = vn;
+        d[c * N + i] = p[c] + cf.tau2 * vn;                     // drift_2
     }
 }
 
@@ -245,7 +474,7 @@ template <int ORDER>
 __global__ void __launch_bounds__(256) k_adj_interp(PmGeom g, const float* __restrict__ disp, float* __restrict__ vel,
                                                     float* __restrict__ adisp, const float* __restrict__ avel,
                                                     const SlotCoef* __restrict__ coef, int cstride,
-                                                    const float* __restrict__ force, float* __restrict__ s3) {
+                                                    const float4* __restrict__ force4, float* __restrict__ s3) {
     const int slot = blockIdx.y;
     const SlotCoef cf = coef[slot * cstride];
     if (!cf.active) return;
@@ -266,7 +495,7 @@ __global__ void __launch_bounds__(256) k_adj_interp(PmGeom g, const float* __res
     const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[2] * g.inv_h);
     const int ng = 1 << g.log2ng, msk = ng - 1;
     const long long M = 1ll << (3 * g.log2ng);
-    const float* f = force + slot * 3 * M;
+    const float4* f = force4 + slot * M;
     float* sm = s3 + slot * 3 * M;
     float A[3] = {0.f, 0.f, 0.f};
     float t[3] = {0.f, 0.f, 0.f};   // sum_c u_c d/du_d gather(g_c)
@@ -280,7 +509,8 @@ __global__ void __launch_bounds__(256) k_adj_interp(PmGeom g, const float* __res
             for (int a = 0; a < ORDER; ++a) {
                 const long long j = yo + ((ax.c + a) & msk);
                 const float w = az.w[c] * ay.w[b] * ax.w[a];
-                const float g0 = __ldg(&f[j]), g1 = __ldg(&f[M + j]), g2 = __ldg(&f[2 * M + j]);
+                const float4 gv = __ldg(&f[j]);
+                const float g0 = gv.x, g1 = gv.y, g2 = gv.z;
                 A[0] += w * g0;
                 A[1] += w * g1;
                 A[2] += w * g2;
@@ -391,6 +621,25 @@ __global__ void k_axpby(float* __restrict__ out, const float* __restrict__ x, co
 int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, const SlotCoef* coef, int coef_stride,
                float shift_cells, float* rho, int nslots, cudaStream_t st) {
     const long long N = 1ll << (3 * g.log2np);
+    const int R = 1 << (g.log2ng - g.log2np > 0 ? g.log2ng - g.log2np : 0);
+    const bool tiled = (g.log2ng - g.log2np == 0 && g.log2np >= 5) || (g.log2ng - g.log2np == 1 && g.log2np >= 4);
+    if (tiled && (order == 2 || order == 3)) {
+        const int np = 1 << g.log2np;
+        const unsigned ntiles = (unsigned)((long long)(np / (32 / R)) * (np / (8 / R)) * (np / (8 / R)));
+        dim3 grid(ntiles, nslots);
+#define PM_DT(O, RR)                                                                                      \
+    {                                                                                                     \
+        const int smem = DepWindow<O>::CELLS * (int)sizeof(unsigned);                                        \
+        cudaFuncSetAttribute(k_deposit_tiled<O, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);  \
+        k_deposit_tiled<O, RR><<<grid, 256, smem, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho); \
+    }
+        if (order == 2 && R == 1) PM_DT(2, 1)
+        else if (order == 2) PM_DT(2, 2)
+        else if (R == 1) PM_DT(3, 1)
+        else PM_DT(3, 2)
+#undef PM_DT
+        return 0;
+    }
     dim3 grid((unsigned)((N + 255) / 256), nslots);
     if (order == 2)
         k_deposit<2><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho);
@@ -402,10 +651,10 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
 }
 
 int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float* vel, const SlotCoef* coef,
-                   int coef_stride, const float* force, int nslots, cudaStream_t st) {
+                   int coef_stride, const float4* force4, int nslots, cudaStream_t st) {
     const long long N = 1ll << (3 * g.log2np);
     dim3 grid((unsigned)((N + 255) / 256), nslots);
-#define PM_IK(O, I) k_interp<O, I, 1><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, force, nullptr)
+#define PM_IK(O, I) k_interp_kick<O, I><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, force4)
     if (order == 2 && !interlace) PM_IK(2, 0);
     else if (order == 2 && interlace) PM_IK(2, 1);
     else if (order == 3 && !interlace) PM_IK(3, 0);
@@ -441,7 +690,7 @@ int pm_adj_drift_deposit(int order, const PmGeom& g, float* disp, const float* v
 }
 
 int pm_adj_interp(int order, const PmGeom& g, const float* disp, float* vel, float* adisp, const float* avel,
-                  const SlotCoef* coef, int cstride, const float* force, float* s3, int nslots, cudaStream_t st) {
+                  const SlotCoef* coef, int cstride, const float4* force, float* s3, int nslots, cudaStream_t st) {
     const long long N = 1ll << (3 * g.log2np);
     dim3 grid((unsigned)((N + 255) / 256), nslots);
     if (order == 2) k_adj_interp<2><<<grid, 256, 0, st>>>(g, disp, vel, adisp, avel, coef, cstride, force, s3);

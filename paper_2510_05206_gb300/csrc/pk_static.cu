@@ -24,14 +24,15 @@ constexpr long long kMeshFloats = (long long)kMaxMesh * kMaxMesh * kMaxMesh;
 constexpr long long kSpecCplx = (long long)kMaxMesh * kMaxMesh * (kMaxMesh / 2 + SPEC_PAD);
 constexpr int kBinTab = 3 * (kMaxMesh / 2) * (kMaxMesh / 2) + 1;
 
-// byte offsets inside the scratch array (each 256-byte aligned)
+// byte offsets inside the scratch array (each 256-byte aligned); the FP64 bin
+// accumulators hold sum w |rho^|^2 per bin
 constexpr long long align256(long long b) { return (b + 255) / 256 * 256; }
 constexpr long long kOffRho = 0;
 constexpr long long kOffSpec = align256(kOffRho + 4 * kMeshFloats);
 constexpr long long kOffTw = align256(kOffSpec + 8 * kSpecCplx);
 constexpr long long kOffBin = align256(kOffTw + 8 * kMaxMesh);
 constexpr long long kOffAcc = align256(kOffBin + 4 * kBinTab);
-constexpr long long kOffCoef = align256(kOffAcc + 8 * 3 * kMaxBins);
+constexpr long long kOffCoef = align256(kOffAcc + 8 * kMaxBins);
 constexpr long long kScratchBytes = align256(kOffCoef + (long long)sizeof(SlotCoef));
 
 static __device__ __align__(256) unsigned char g_pk_scratch[kScratchBytes];
@@ -106,7 +107,7 @@ extern "C" int pm_power_spectrum_static(const float* disp, int32_t n_part, doubl
     // the array keeps the previous call's contents: clear what accumulates
     cudaMemsetAsync(rho, 0, sizeof(float) * M, st);
     cudaMemsetAsync(spec, 0, sizeof(float2) * S, st);
-    cudaMemsetAsync(acc, 0, sizeof(double) * 3 * n_bins, st);
+    cudaMemsetAsync(acc, 0, sizeof(double) * n_bins, st);
     k_static_tables<<<(ns + 255) / 256, 256, 0, st>>>(tw, n, bintab, ns, n_bins, coef);
     PmGeom g;
     g.log2np = ilog2s(n_part);
@@ -125,20 +126,35 @@ extern "C" int pm_power_spectrum_static(const float* disp, int32_t n_part, doubl
     z.pk_out = acc;
     z.nbins = n_bins;
     pm_fft_z(l2, PM_Z_PK, z, 1, st);
-    double h_acc[3 * kMaxBins];
+    double h_acc[kMaxBins];
     if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(h_acc, acc, sizeof(double) * 3 * n_bins, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(h_acc, acc, sizeof(double) * n_bins, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return PM_ERR_CUDA;
     }
+    // exact mode counts and |m| sums of each bin (full n^3 grid through the half spectrum)
+    double cnt[kMaxBins] = {}, ksum[kMaxBins] = {};
+    for (int kx = 0; kx <= n / 2; ++kx) {
+        const double w = (kx == 0 || kx == n / 2) ? 1.0 : 2.0;
+        for (int y = 0; y < n; ++y) {
+            const int my = y < n / 2 ? y : y - n;
+            for (int zz = 0; zz < n; ++zz) {
+                const int mz = zz < n / 2 ? zz : zz - n;
+                const int sq = kx * kx + my * my + mz * mz;
+                const int b = (int)std::floor(std::sqrt((double)sq) - 0.5);
+                if (sq == 0 || b < 0 || b >= n_bins) continue;
+                cnt[b] += w;
+                ksum[b] += w * std::sqrt((double)sq);
+            }
+        }
+    }
     const double N = (double)n_part * n_part * n_part;
     const double kf = 2.0 * M_PI / box, MN = (double)M / N;
     for (int i = 0; i < n_bins; ++i) {
-        const double cnt = h_acc[2 * n_bins + i];
-        n_modes[i] = (int64_t)std::llround(cnt);
-        k[i] = cnt > 0 ? h_acc[n_bins + i] / cnt * kf : 0.0;
-        pk[i] = cnt > 0 ? h_acc[i] / cnt * MN * MN * box * box * box / ((double)M * (double)M) : 0.0;
+        n_modes[i] = (int64_t)std::llround(cnt[i]);
+        k[i] = cnt[i] > 0 ? ksum[i] / cnt[i] * kf : 0.0;
+        pk[i] = cnt[i] > 0 ? h_acc[i] / cnt[i] * MN * MN * box * box * box / ((double)M * (double)M) : 0.0;
     }
     return PM_OK;
 }

@@ -48,7 +48,7 @@ struct pm_handle {
     // device workspace
     float* rho = nullptr;        // [B][ngrids][max(Mg, Mpk)]
     float2* spec = nullptr;      // [B][ncomp][spec_elems(nmax)]
-    float* force = nullptr;      // [B][ncomp][Mg]
+    float4* force = nullptr;     // [B][ngrids][Mg] interleaved (gx, gy, gz, 0)
     SlotCoef* d_table = nullptr; // [n_steps]
     SlotCoef* d_slots = nullptr; // [B]
     SlotCoef* d_unit = nullptr;  // active, tau1 = 0
@@ -56,9 +56,13 @@ struct pm_handle {
     float* d_lap = nullptr;      // [ng]
     float* d_grad = nullptr;     // [ng]
     float* d_ictab = nullptr;    // [3 (np/2)^2 + 1]
-    double* d_pk = nullptr;      // [B][3][pk_bins_cap]
+    double* d_pk = nullptr;      // [B][pk_bins_cap]: sum over each bin of w |rho^|^2
     int pk_bins_cap = 0;
-    std::map<std::pair<int, int>, int*> d_bintab;   // (n, nbins) -> table
+    struct BinTable {
+        int* d_tab = nullptr;                       // bin of every integer |m|^2 (-1 = none)
+        std::vector<double> count, ksum;            // exact per-bin mode counts and sum |m|
+    };
+    std::map<std::pair<int, int>, BinTable> bintabs;   // (n, nbins)
     // slot mode
     SlotCoef* h_slots = nullptr; // pinned ring [4][B]
     cudaEvent_t slot_ev[4] = {};
@@ -187,7 +191,7 @@ size_t workspace_bytes(const pm_config* c) {
     size_t b = 0;
     b += (size_t)c->batch * ngrids * std::max(mesh_elems(ng), mesh_elems(npk)) * 4;
     b += (size_t)c->batch * ncomp * spec_elems(nmax) * 8;
-    b += (size_t)c->batch * ncomp * mesh_elems(ng) * 4;
+    b += (size_t)c->batch * ngrids * mesh_elems(ng) * 16;
     b += (size_t)(3 * (np / 2) * (np / 2) + 1) * 4 + 8 * 1024 * 8 * 2 + (size_t)ng * 8;
     b += (size_t)(c->n_steps + c->batch + 1) * sizeof(SlotCoef);
     return b;
@@ -233,7 +237,7 @@ PmGeom geom(const pm_handle* h, int nmesh, long long slot_mesh) {
 // Forward real FFT of ngrids density meshes per slot (rho, slot stride rho_slot)
 // into spectra comp 0..ngrids-1; then the fused z pass producing ncomp spectra.
 int spectral_force(pm_handle* h, const float* src, long long src_slot, long long src_grid, float scale,
-                   float* force_out, int nslots) {
+                   float* force_out, float4* force4, int nslots) {
     const int n = h->ng, l2 = ilog2i(n);
     const long long S = spec_elems(n), SS = (long long)h->ncomp * S;
     cudaStream_t st = h->stream;
@@ -261,8 +265,14 @@ int spectral_force(pm_handle* h, const float* src, long long src_slot, long long
     h->phase(4, 1);
     pm_fft_y(l2, h->spec, S, nslots * h->ncomp, 1, h->d_tw[l2], st);
     h->phase_end();
-    h->phase(5, 1);
-    pm_fft_c2r_x(l2, h->spec, S, force_out, h->Mg(), nullptr, 0, 0.f, nslots * h->ncomp, h->d_tw[l2], st);
+    h->phase(5, force4 ? h->ngrids : 1);
+    if (force4) {
+        for (int g = 0; g < h->ngrids; ++g)
+            pm_fft_c2r_x3(l2, h->spec + 3 * g * S, S, SS, force4 + g * h->Mg(), (long long)h->ngrids * h->Mg(), nslots,
+                          h->d_tw[l2], st);
+    } else {
+        pm_fft_c2r_x(l2, h->spec, S, force_out, h->Mg(), nullptr, 0, 0.f, nslots * h->ncomp, h->d_tw[l2], st);
+    }
     h->phase_end();
     return h->check_launch("force spectral passes");
 }
@@ -283,32 +293,50 @@ int one_step(pm_handle* h, float* disp, float* vel, const SlotCoef* coef, int cs
     h->phase_end();
     // delta = rho M/N - 1; the -1 only touches k = 0 (zeroed), and M/N with the
     // 1/M of the inverse transform leaves 1/N on the multiplier
-    int rc = spectral_force(h, h->rho, h->rho_slot(), Mg, (float)(1.0 / (double)h->Np()), h->force, h->B);
+    int rc = spectral_force(h, h->rho, h->rho_slot(), Mg, (float)(1.0 / (double)h->Np()), nullptr, h->force, h->B);
     if (rc) return rc;
-    const PmGeom gi = geom(h, h->ng, (long long)h->ncomp * Mg);
+    const PmGeom gi = geom(h, h->ng, (long long)h->ngrids * Mg);
     h->phase(6, 1);
     pm_interp_kick(h->cfg.order, h->cfg.interlace, gi, disp, vel, coef, cstride, h->force, h->B, st);
     h->phase_end();
     return h->check_launch("pm step");
 }
 
-int bintab_for(pm_handle* h, int n, int nbins, int** out) {
+int bintab_for(pm_handle* h, int n, int nbins, const pm_handle::BinTable** out) {
     auto key = std::make_pair(n, nbins);
-    auto it = h->d_bintab.find(key);
-    if (it != h->d_bintab.end()) { *out = it->second; return PM_OK; }
+    auto it = h->bintabs.find(key);
+    if (it != h->bintabs.end()) { *out = &it->second; return PM_OK; }
     const int ns = 3 * (n / 2) * (n / 2) + 1;
     std::vector<int> t(ns);
     for (int s = 0; s < ns; ++s) {
         const int b = (int)std::floor(std::sqrt((double)s) - 0.5);
         t[s] = (s > 0 && b >= 0 && b < nbins) ? b : -1;
     }
-    int* d = nullptr;
-    int rc = dalloc(h, &d, ns, "P(k) bin table");
+    pm_handle::BinTable bt;
+    bt.count.assign(nbins, 0.0);
+    bt.ksum.assign(nbins, 0.0);
+    // modes of the full n^3 grid, counted through the half spectrum kx = 0..n/2
+    // (weight 2 for 0 < kx < n/2: the mode and its mirror -k)
+    for (int kx = 0; kx <= n / 2; ++kx) {
+        const double w = (kx == 0 || kx == n / 2) ? 1.0 : 2.0;
+        for (int y = 0; y < n; ++y) {
+            const int my = y < n / 2 ? y : y - n;
+            for (int z = 0; z < n; ++z) {
+                const int mz = z < n / 2 ? z : z - n;
+                const int sq = kx * kx + my * my + mz * mz;
+                const int b = t[sq];
+                if (b < 0) continue;
+                bt.count[b] += w;
+                bt.ksum[b] += w * std::sqrt((double)sq);
+            }
+        }
+    }
+    int rc = dalloc(h, &bt.d_tab, ns, "P(k) bin table");
     if (rc) return rc;
-    if (cudaMemcpy(d, t.data(), ns * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(bt.d_tab, t.data(), ns * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         return h->fail(PM_ERR_CUDA, "upload bin table");
-    h->d_bintab[key] = d;
-    *out = d;
+    auto res = h->bintabs.emplace(key, std::move(bt));
+    *out = &res.first->second;
     return PM_OK;
 }
 
@@ -400,7 +428,7 @@ int pm_init(const pm_config* cfg, void* stream, pm_handle** out) {
     const int B = h->B;
     if ((rc = dalloc(h.get(), &h->rho, (size_t)B * h->rho_slot(), "density"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->spec, (size_t)B * h->spec_slot(), "spectra"))) return bail(rc);
-    if ((rc = dalloc(h.get(), &h->force, (size_t)B * h->ncomp * h->Mg(), "force meshes"))) return bail(rc);
+    if ((rc = dalloc(h.get(), &h->force, (size_t)B * h->ngrids * h->Mg(), "force meshes"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->d_table, (size_t)cfg->n_steps, "step table"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->d_slots, (size_t)B, "slot table"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->d_unit, 1, "unit coef"))) return bail(rc);
@@ -486,7 +514,7 @@ void pm_destroy(pm_handle* h) {
     cudaFree(h->d_grad);
     cudaFree(h->d_ictab);
     cudaFree(h->d_pk);
-    for (auto& kv : h->d_bintab) cudaFree(kv.second);
+    for (auto& kv : h->bintabs) cudaFree(kv.second.d_tab);
     cudaFree(h->adj3);
     cudaFree(h->d_dot);
     cudaFree(h->d_noise);
@@ -618,16 +646,16 @@ int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n, int32_t nbins,
     if (nbins > h->pk_bins_cap) {
         cudaFree(h->d_pk);
         h->d_pk = nullptr;
-        if ((rc = dalloc(h, &h->d_pk, (size_t)h->B * 3 * nbins, "P(k) bins"))) return rc;
+        if ((rc = dalloc(h, &h->d_pk, (size_t)h->B * nbins, "P(k) bins"))) return rc;
         h->pk_bins_cap = nbins;
     }
-    int* bintab = nullptr;
-    if ((rc = bintab_for(h, n, nbins, &bintab))) return rc;
+    const pm_handle::BinTable* bt = nullptr;
+    if ((rc = bintab_for(h, n, nbins, &bt))) return rc;
     cudaStream_t st = h->stream;
     const int l2 = ilog2i(n);
-    const long long M = mesh_elems(n), S = spec_elems(n);
+    const long long M = mesh_elems(n);
     cudaMemsetAsync(h->rho, 0, sizeof(float) * h->rho_slot() * h->B, st);
-    cudaMemsetAsync(h->d_pk, 0, sizeof(double) * h->B * 3 * nbins, st);
+    cudaMemsetAsync(h->d_pk, 0, sizeof(double) * h->B * nbins, st);
     h->phase(8, 4);
     pm_deposit(2, geom(h, n, h->rho_slot()), disp, nullptr, h->d_unit, 0, 0.f, h->rho, h->B, st);
     pm_fft_r2c_x(l2, h->rho, h->rho_slot(), h->spec, h->spec_slot(), h->B, h->d_tw[l2], st);
@@ -636,27 +664,25 @@ int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n, int32_t nbins,
     z.in[0] = h->spec;
     z.slot_stride = h->spec_slot();
     z.tw = h->d_tw[l2];
-    z.bintab = bintab;
+    z.bintab = bt->d_tab;
     z.pk_out = h->d_pk;
     z.nbins = nbins;
     pm_fft_z(l2, PM_Z_PK, z, h->B, st);
     h->phase_end();
     if ((rc = h->check_launch("power spectrum"))) return rc;
-    std::vector<double> acc((size_t)h->B * 3 * nbins);
+    std::vector<double> acc((size_t)h->B * nbins);
     if (cudaMemcpyAsync(acc.data(), h->d_pk, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return h->fail(PM_ERR_CUDA, "power spectrum readback: %s", cudaGetErrorString(cudaGetLastError()));
-    (void)S;
     const double L = h->cfg.box, kf = 2.0 * M_PI / L;
     const double MN = (double)M / (double)h->Np();            // delta^ = (M/N) rho^ for k != 0
     for (int b = 0; b < h->B; ++b) {
-        const double* a = acc.data() + (size_t)b * 3 * nbins;
         for (int i = 0; i < nbins; ++i) {
-            const double cnt = a[2 * nbins + i];
+            const double cnt = bt->count[i];
             const size_t o = (size_t)b * nbins + i;
             nmodes[o] = (int64_t)std::llround(cnt);
-            k[o] = cnt > 0 ? a[nbins + i] / cnt * kf : 0.0;
-            pk[o] = cnt > 0 ? a[i] / cnt * MN * MN * L * L * L / ((double)M * (double)M) : 0.0;
+            k[o] = cnt > 0 ? bt->ksum[i] / cnt * kf : 0.0;
+            pk[o] = cnt > 0 ? acc[o] / cnt * MN * MN * L * L * L / ((double)M * (double)M) : 0.0;
         }
     }
     return PM_OK;
@@ -680,7 +706,7 @@ int pm_force_mesh(pm_handle* h, const float* delta, float* force) {
     if (!h) return PM_ERR_ARG;
     if (!delta || !force) return h->fail(PM_ERR_ARG, "pm_force_mesh: NULL buffer");
     if (h->ngrids != 1) return h->fail(PM_ERR_UNSUPPORTED, "pm_force_mesh: single grid only");
-    return spectral_force(h, delta, h->Mg(), 0, (float)(1.0 / (double)h->Mg()), force, h->B);
+    return spectral_force(h, delta, h->Mg(), 0, (float)(1.0 / (double)h->Mg()), force, nullptr, h->B);
 }
 
 int pm_interp(pm_handle* h, const float* disp, const float* force, float* acc) {
@@ -719,7 +745,8 @@ int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adisp, float* avel,
         h->phase(0, 1);
         pm_adj_drift_deposit(order, gd, disp, vel, adisp, avel, coef, 0, h->rho, h->B, st);
         h->phase_end();
-        if ((rc = spectral_force(h, h->rho, h->rho_slot(), Mg, (float)(1.0 / (double)h->Np()), h->force, h->B)))
+        if ((rc = spectral_force(h, h->rho, h->rho_slot(), Mg, (float)(1.0 / (double)h->Np()), nullptr, h->force,
+                                 h->B)))
             return rc;
         cudaMemsetAsync(h->adj3, 0, sizeof(float) * 3 * Mg * h->B, st);
         h->phase(6, 1);

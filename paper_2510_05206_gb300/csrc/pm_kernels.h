@@ -14,7 +14,7 @@ struct PmZPass {
     const float* grad1;
     const float* ictab;
     const int* bintab;
-    double* pk_out;
+    double* pk_out;         // P(k): [slot][nbins] sums of w |delta^|^2
     int nbins;
     float scale;
     float kf;
@@ -26,6 +26,10 @@ int pm_fft_r2c_x(int log2n, const float* in, long long in_stride, float2* out, l
                  const float2* tw, cudaStream_t st);
 int pm_fft_c2r_x(int log2n, const float2* in, long long in_stride, float* out, long long out_stride, float* out2,
                  long long out2_stride, float scale2, int nmesh, const float2* tw, cudaStream_t st);
+// inverse x pass of three spectra (comp_stride apart; slot q at q * slot_stride) into one
+// interleaved float4 mesh (gx, gy, gz, 0) per q (out_stride float4 apart)
+int pm_fft_c2r_x3(int log2n, const float2* in, long long comp_stride, long long slot_stride, float4* out,
+                  long long out_stride, int nmesh, const float2* tw, cudaStream_t st);
 int pm_fft_y(int log2n, float2* data, long long stride, int nmesh, int dir, const float2* tw, cudaStream_t st);
 int pm_fft_z(int log2n, int mode, const PmZPass& p, int nslots, cudaStream_t st);
 
@@ -42,9 +46,10 @@ struct PmGeom {
 int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, const SlotCoef* coef,
                int coef_stride, float shift_cells, float* rho, int nslots, cudaStream_t st);
 // A = gather(g) / D_half^2 at X_half = q + disp + tau1 vel; V' = alpha V + kick A; disp' = disp + tau1 V + tau2 V'.
-// force: [slot][3 or 6][M] (6 with an interlaced second grid at +1/2 cell).
+// force4: [slot][1 or 2 grids][M] float4 (gx, gy, gz, 0); the second grid is shifted by +1/2 cell.
+// g.slot_mesh counts float4 per slot here.
 int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float* vel, const SlotCoef* coef,
-                   int coef_stride, const float* force, int nslots, cudaStream_t st);
+                   int coef_stride, const float4* force4, int nslots, cudaStream_t st);
 // acc[b][c][i] = sum_j g_c,j W(r_j - X_i) at X = q + disp (no kick): stage-level interpolation.
 int pm_interp(int order, int interlace, const PmGeom& g, const float* disp, const float* force, float* acc,
               int nslots, cudaStream_t st);
@@ -53,7 +58,7 @@ int pm_interp(int order, int interlace, const PmGeom& g, const float* disp, cons
 int pm_adj_drift_deposit(int order, const PmGeom& g, float* disp, const float* vel, const float* adisp, float* avel,
                          const SlotCoef* coef, int cstride, float* rho, int nslots, cudaStream_t st);
 int pm_adj_interp(int order, const PmGeom& g, const float* disp, float* vel, float* adisp, const float* avel,
-                  const SlotCoef* coef, int cstride, const float* force, float* s3, int nslots, cudaStream_t st);
+                  const SlotCoef* coef, int cstride, const float4* force4, float* s3, int nslots, cudaStream_t st);
 int pm_adj_gather_grad(int order, int finish, const PmGeom& g, float* disp, const float* vel, float* adisp,
                        float* avel, const SlotCoef* coef, int cstride, const float* rhoa, float scale, int nslots,
                        cudaStream_t st);
