@@ -167,6 +167,29 @@ def cpu_baseline_sample():
                       f"(numpy FP64, single thread; {dt:.1f} s)"}
 
 
+def serving_benchmark(n_req, dev):
+    """Continuous batching of a seeded Poisson stream of PM requests (sizes
+    64^3 / 128^3 / 256^3 particles = mesh cells, L = 2 Mpc/h per cell, 4-10
+    BullFrog steps), offered at the sequential service capacity, against the
+    same stream served one request at a time on the same GPU."""
+    from paper_2510_05206_gb300 import serve
+    sizes, steps = (64, 128, 256), (4, 10)
+    # sequential capacity: all requests of a calibration stream at t = 0
+    cal = serve.make_stream(48, sizes, steps, rate=1e9, seed=18)
+    serve.serve_sequential(cal[:6], device=dev)            # warm-up (first launches, tables)
+    _, wall = serve.serve_sequential(cal, device=dev)
+    capacity = len(cal) / wall
+    reqs = serve.make_stream(n_req, sizes, steps, rate=capacity, seed=8)
+    done, wall_b = serve.serve(reqs, device=dev)
+    batched = serve.latency_stats(done, wall_b)
+    reqs = serve.make_stream(n_req, sizes, steps, rate=capacity, seed=8)
+    done, wall_s = serve.serve_sequential(reqs, device=dev)
+    sequential = serve.latency_stats(done, wall_s)
+    return {"requests": n_req, "offered_rate_per_s": capacity, "sizes": list(sizes), "steps": list(steps),
+            "batched": batched, "sequential": sequential,
+            "note": "arrival rate = measured sequential capacity; latency = arrival -> final state in host memory"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -177,6 +200,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--size", type=int, default=512, help="particles per dimension (512 = the benchmark workload)")
     ap.add_argument("--mesh", type=int, default=0, help="mesh cells per dimension (default = --size)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the continuous-batching measurement")
+    ap.add_argument("--serve-requests", type=int, default=256)
     args = ap.parse_args()
     if args.size != 512 or (args.mesh and args.mesh != 512):
         # a reduced case for profiling captures; the config says so
@@ -291,6 +316,8 @@ def main():
             "e2e": e2e,
             "clocks": clock_info,
             "ms_per_pm_step": ms / args.steps / cfg.n_steps}
+    if not args.no_serving:
+        line["serving"] = serving_benchmark(args.serve_requests, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
     if rank == 0:
