@@ -179,15 +179,22 @@ def serving_benchmark(n_req, dev):
     serve.serve_sequential(cal[:6], device=dev)            # warm-up (first launches, tables)
     _, wall = serve.serve_sequential(cal, device=dev)
     capacity = len(cal) / wall
-    reqs = serve.make_stream(n_req, sizes, steps, rate=capacity, seed=8)
-    done, wall_b = serve.serve(reqs, device=dev)
-    batched = serve.latency_stats(done, wall_b)
-    reqs = serve.make_stream(n_req, sizes, steps, rate=capacity, seed=8)
-    done, wall_s = serve.serve_sequential(reqs, device=dev)
-    sequential = serve.latency_stats(done, wall_s)
-    return {"requests": n_req, "offered_rate_per_s": capacity, "sizes": list(sizes), "steps": list(steps),
-            "batched": batched, "sequential": sequential,
-            "note": "arrival rate = measured sequential capacity; latency = arrival -> final state in host memory"}
+    cal = serve.make_stream(96, sizes, steps, rate=1e9, seed=19)
+    _, wall_cb = serve.serve(cal, device=dev)
+    cap_batched = len(cal) / wall_cb
+    out = {"requests": n_req, "sizes": list(sizes), "steps": list(steps),
+           "capacity_req_per_s": {"batched": cap_batched, "sequential": capacity},
+           "note": "capacity: all requests at t = 0; loads: Poisson arrivals at the given multiple of the "
+                   "sequential capacity; latency = arrival -> final state in host memory"}
+    for mult in (1.0, 2.0):
+        reqs = serve.make_stream(n_req, sizes, steps, rate=mult * capacity, seed=8)
+        done, wall_b = serve.serve(reqs, device=dev)
+        reqs = serve.make_stream(n_req, sizes, steps, rate=mult * capacity, seed=8)
+        done_s, wall_s = serve.serve_sequential(reqs, device=dev)
+        out[f"load_{mult:g}x"] = {"offered_rate_per_s": mult * capacity,
+                                  "batched": serve.latency_stats(done, wall_b),
+                                  "sequential": serve.latency_stats(done_s, wall_s)}
+    return out
 
 
 def main():

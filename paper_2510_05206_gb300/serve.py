@@ -68,6 +68,7 @@ class SizeClass:
         self.B = slots
         self.device = device
         self.stream = torch.cuda.Stream(device=device)
+        self.copy_stream = torch.cuda.Stream(device=device)   # result copies overlap the next steps
         with torch.cuda.stream(self.stream):
             self.pm = pmmod.PM(class_config(n, slots), device=device)
             self.disp, self.vel = self.pm.new_state()
@@ -126,17 +127,21 @@ class SizeClass:
         copies of finished slots.  Returns True if a step completed."""
         if self.pending is None or not self.pending.query():
             return False
+        step_ev = self.pending
         self.pending = None
         for i in range(self.B):
             if self.req[i] is None or self.step[i] < 0:
                 continue
             self.step[i] += 1
             if self.step[i] >= self.nsteps[i]:
-                with torch.cuda.stream(self.stream):
+                # the slot is idle for the kernels from now on (inactive coefficients), so its
+                # state can be copied on the copy stream while the other slots keep stepping
+                self.copy_stream.wait_event(step_ev)
+                with torch.cuda.stream(self.copy_stream):
                     self.host_disp[i].copy_(self.disp[i], non_blocking=True)
                     self.host_vel[i].copy_(self.vel[i], non_blocking=True)
                     ev = torch.cuda.Event()
-                    ev.record(self.stream)
+                    ev.record(self.copy_stream)
                 self.retiring.append((ev, self.req[i], i))
                 self.step[i] = -1          # the slot stays held until its copy completes
         return True
@@ -157,7 +162,7 @@ class SizeClass:
         return done
 
 
-def slots_for_budget(sizes, budget_bytes, max_slots=(32, 16, 8)):
+def slots_for_budget(sizes, budget_bytes, max_slots=(32, 16, 4)):
     """Slots per size class: the largest counts (up to max_slots) whose state
     plus libpmgb workspace fit in an equal share of the HBM budget (admission
     control by device memory)."""
