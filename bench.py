@@ -106,13 +106,16 @@ def algorithmic_bytes(n_part, n_mesh):
     N = particles; complex half spectra count as M/2 complex = 4M bytes)."""
     N, M = n_part ** 3, n_mesh ** 3
     return {
-        "deposit": 24 * N + 4 * M,               # read disp, vel; write the density once
+        # deposit: the first step of a run reads disp and vel (24 N), the later ones
+        # the carried pre-drifted positions only (12 N): 14 N per launch on average over
+        # 6 steps; the density is written once (4 M)
+        "deposit": 14 * N + 4 * M,
         "fft_x_fwd": 4 * M + 4 * M,              # read real mesh, write half spectrum
         "fft_y_fwd": 8 * M,                      # read + write half spectrum
         "fft_z_green": 4 * M + 12 * M,           # read 1 spectrum, write 3
         "fft_y_inv": 3 * 8 * M,                  # 3 spectra in place
-        "fft_x_inv": 12 * M + 12 * M,            # 3 spectra -> 3 real force meshes
-        "interp_kick_drift": 48 * N + 12 * M,    # read disp, vel, 3 force meshes; write disp, vel
+        "fft_x_inv": 12 * M + 12 * M,            # 3 spectra -> 3 force components (stored as float4: padding not counted)
+        "interp_kick_drift": 48 * N + 12 * M,    # read disp, vel, 3 force components; write disp, vel
     }
 
 

@@ -272,22 +272,23 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
             const int e = i / COL_TILE, l = i % COL_TILE;
             const int kx = kx0 + l;
             int b = -1;
-            double v = 0.0;
+            float v = 0.f;
             if (kx <= n / 2) {
                 const int mz = freq_index(e, n);
-                b = a.bintab[kx * kx + my * my + mz * mz];
+                b = __ldg(&a.bintab[kx * kx + my * my + mz * mz]);
                 const float2 d = A(l, e);
-                v = ((kx == 0 || kx == n / 2) ? 1.0 : 2.0) * ((double)d.x * d.x + (double)d.y * d.y);
+                v = ((kx == 0 || kx == n / 2) ? 1.f : 2.f) * (d.x * d.x + d.y * d.y);
             }
+            // the float sum of at most 32 lanes feeds an FP64 per-bin accumulator
             unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
             while (todo) {
                 const int leader = __ffs(todo) - 1;
                 const int bl = __shfl_sync(0xffffffffu, b, leader);
                 const bool mine = (b == bl);
-                double sv = mine ? v : 0.0;
+                float sv = mine ? v : 0.f;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-                if (lane == leader) atomicAdd(&acc[bl], sv);
+                if (lane == leader) atomicAdd(&acc[bl], (double)sv);
                 todo &= ~__ballot_sync(0xffffffffu, mine);
             }
         }

@@ -109,6 +109,62 @@ __global__ void __launch_bounds__(256) k_deposit(PmGeom g, const float* __restri
 }
 
 
+// sum over taps of g_c at the particle, c = 0..2, meshes at f, f + M, f + 2M
+template <int ORDER>
+__device__ __forceinline__ void gather3(const float* __restrict__ f, long long M, int log2ng, const AxisTaps& ax,
+                                        const AxisTaps& ay, const AxisTaps& az, float acc[3]) {
+    const int ng = 1 << log2ng, msk = ng - 1;
+#pragma unroll
+    for (int c = 0; c < ORDER; ++c) {
+        const long long zo = (long long)((az.c + c) & msk) * ng;
+#pragma unroll
+        for (int b = 0; b < ORDER; ++b) {
+            const long long yo = (zo + ((ay.c + b) & msk)) * ng;
+            const float wzy = az.w[c] * ay.w[b];
+#pragma unroll
+            for (int a = 0; a < ORDER; ++a) {
+                const long long j = yo + ((ax.c + a) & msk);
+                const float w = wzy * ax.w[a];
+                acc[0] += w * __ldg(&f[j]);
+                acc[1] += w * __ldg(&f[M + j]);
+                acc[2] += w * __ldg(&f[2 * M + j]);
+            }
+        }
+    }
+}
+
+// L2 prefetch of the 128-byte line holding p (no registers held, nothing returned)
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// particles ahead of the current ones whose state lines each warp prefetches into L2:
+// about the number of particles resident on the GPU at once, so that their state
+// arrives while the current ones wait on their force gathers
+constexpr long long STATE_PREFETCH = 1ll << 17;
+
+// same from an interleaved float4 mesh (gx, gy, gz, 0): one 16-byte load per tap
+template <int ORDER>
+__device__ __forceinline__ void gather3v(const float4* __restrict__ f, int log2ng, const AxisTaps& ax,
+                                         const AxisTaps& ay, const AxisTaps& az, float acc[3]) {
+    const int ng = 1 << log2ng, msk = ng - 1;
+#pragma unroll
+    for (int c = 0; c < ORDER; ++c) {
+        const long long zo = (long long)((az.c + c) & msk) * ng;
+#pragma unroll
+        for (int b = 0; b < ORDER; ++b) {
+            const long long yo = (zo + ((ay.c + b) & msk)) * ng;
+            const float wzy = az.w[c] * ay.w[b];
+#pragma unroll
+            for (int a = 0; a < ORDER; ++a) {
+                const float4 v = __ldg(&f[yo + ((ax.c + a) & msk)]);
+                const float w = wzy * ax.w[a];
+                acc[0] += w * v.x;
+                acc[1] += w * v.y;
+                acc[2] += w * v.z;
+            }
+        }
+    }
+}
+
 // Lagrangian-tile deposit through a shared-memory window.
 // A CTA owns a tile of (32/R) x (8/R) x (8/R) lattice sites (R = n_mesh / n_part in
 // {1, 2}), i.e. a 32 x 8 x 8 block of cells.  Pass 1 loads the tile's
@@ -142,52 +198,36 @@ __device__ __forceinline__ void red_v4(float* p, float4 v) {
                  : "memory");
 }
 
-template <int ORDER, int R>
-__global__ void __launch_bounds__(256) k_deposit_tiled(PmGeom g, const float* __restrict__ disp,
-                                                       const float* __restrict__ vel,
-                                                       const SlotCoef* __restrict__ coef, int cstride, float shift,
-                                                       float* __restrict__ rho) {
-    using Win = DepWindow<ORDER>;
-    constexpr int TXP = 32 / R, TYP = 8 / R, TZP = 8 / R;
-    constexpr int PPT = TXP * TYP * TZP / 256;          // particles per thread
-    constexpr int RSTEP = 256 / TXP;                     // rows advanced per particle slot
-    extern __shared__ unsigned win[];
-    __shared__ float red[3][8];
-    const int slot = blockIdx.y;
-    const SlotCoef cf = coef[slot * cstride];
-    if (!cf.active) return;
-    const int np = 1 << g.log2np;
-    const int ntx = np / TXP, nty = np / TYP;
-    const int tile = blockIdx.x;
-    const int ix0 = (tile % ntx) * TXP;
-    const int iy0 = ((tile / ntx) % nty) * TYP;
-    const int iz0 = (tile / (ntx * nty)) * TZP;
-    const long long N = 1ll << (3 * g.log2np);
-    const float* d = disp + slot * g.slot_part;
-    const float* v = vel ? vel + slot * g.slot_part : nullptr;
-    const int t = threadIdx.x;
-    const int xp = t % TXP;
-
-    // pass 1: drifted displacements in cells, and the tile mean
-    float sx[PPT], sy[PPT], sz[PPT];
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-#pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-        const int row = t / TXP + RSTEP * p;
-        const long long i = ((long long)(iz0 + row / TYP) * np + (iy0 + row % TYP)) * np + (ix0 + xp);
-        float a = d[i], b = d[N + i], c = d[2 * N + i];
-        if (v) {
-            a += cf.tau1 * v[i];
-            b += cf.tau1 * v[N + i];
-            c += cf.tau1 * v[2 * N + i];
-        }
-        sx[p] = a * g.inv_h + shift;
-        sy[p] = b * g.inv_h + shift;
-        sz[p] = c * g.inv_h + shift;
-        m0 += sx[p];
-        m1 += sy[p];
-        m2 += sz[p];
+// Tile geometry of the Lagrangian-tile kernels (R = n_mesh / n_part in {1, 2}).
+template <int R>
+struct TileGeom {
+    static constexpr int TXP = 32 / R, TYP = 8 / R, TZP = 8 / R;
+    static constexpr int PPT = TXP * TYP * TZP / 256;    // particles per thread
+    static constexpr int RSTEP = 256 / TXP;               // rows advanced per particle slot
+    int ix0, iy0, iz0, xp;
+    __device__ TileGeom(int tile, int np) {
+        const int ntx = np / TXP, nty = np / TYP;
+        ix0 = (tile % ntx) * TXP;
+        iy0 = ((tile / ntx) % nty) * TYP;
+        iz0 = (tile / (ntx * nty)) * TZP;
+        xp = threadIdx.x % TXP;
     }
+    __device__ int iy(int p) const { return iy0 + (threadIdx.x / TXP + RSTEP * p) % TYP; }
+    __device__ int iz(int p) const { return iz0 + (threadIdx.x / TXP + RSTEP * p) / TYP; }
+    __device__ long long index(int p, int np) const { return ((long long)iz(p) * np + iy(p)) * np + (ix0 + xp); }
+};
+
+// Second half of a tile deposit: the tile mean of the displacements in cells
+// (m0..m2 hold this thread's partial sums), the window placement, the scatter
+// of the thread's PPT particles into the window (or into global memory when
+// their taps leave it), and the flush.  Called by all 256 threads.
+template <int ORDER, int R>
+__device__ __forceinline__ void tile_window_deposit(const PmGeom& g, const TileGeom<R>& T, const float* sx,
+                                                    const float* sy, const float* sz, float m0, float m1, float m2,
+                                                    unsigned* win, float (*red)[8], float* __restrict__ m) {
+    using Win = DepWindow<ORDER>;
+    constexpr int PPT = TileGeom<R>::PPT;
+    const int t = threadIdx.x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         m0 += __shfl_xor_sync(0xffffffffu, m0, o);
@@ -207,22 +247,18 @@ __global__ void __launch_bounds__(256) k_deposit_tiled(PmGeom g, const float* __
         float sum = 0.f;
 #pragma unroll
         for (int w = 0; w < 8; ++w) sum += red[c][w];
-        mean[c] = sum * (1.f / (TXP * TYP * TZP));
+        mean[c] = sum * (1.f / (TileGeom<R>::TXP * TileGeom<R>::TYP * TileGeom<R>::TZP));
     }
-    const int ox = (ix0 * R + __float2int_rn(mean[0]) - TILE_HALO - Win::LO) & ~3;
-    const int oy = iy0 * R + __float2int_rn(mean[1]) - TILE_HALO - Win::LO;
-    const int oz = iz0 * R + __float2int_rn(mean[2]) - TILE_HALO - Win::LO;
+    const int ox = (T.ix0 * R + __float2int_rn(mean[0]) - TILE_HALO - Win::LO) & ~3;
+    const int oy = T.iy0 * R + __float2int_rn(mean[1]) - TILE_HALO - Win::LO;
+    const int oz = T.iz0 * R + __float2int_rn(mean[2]) - TILE_HALO - Win::LO;
     const int ng = 1 << g.log2ng, msk = ng - 1;
-    float* m = rho + slot * g.slot_mesh;
     const int ds = g.log2ng - g.log2np;
-
-    // pass 2: scatter into the window (or straight to global memory)
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-        const int row = t / TXP + RSTEP * p;
-        const AxisTaps ax = axis_taps<ORDER>(ix0 + xp, ds, sx[p]);
-        const AxisTaps ay = axis_taps<ORDER>(iy0 + row % TYP, ds, sy[p]);
-        const AxisTaps az = axis_taps<ORDER>(iz0 + row / TYP, ds, sz[p]);
+        const AxisTaps ax = axis_taps<ORDER>(T.ix0 + T.xp, ds, sx[p]);
+        const AxisTaps ay = axis_taps<ORDER>(T.iy(p), ds, sy[p]);
+        const AxisTaps az = axis_taps<ORDER>(T.iz(p), ds, sz[p]);
         const int lx = ax.c - ox, ly = ay.c - oy, lz = az.c - oz;
         const bool inside = lx >= 0 && lx + ORDER <= Win::WX && ly >= 0 && ly + ORDER <= Win::WY && lz >= 0 &&
                             lz + ORDER <= Win::WZ;
@@ -251,7 +287,6 @@ __global__ void __launch_bounds__(256) k_deposit_tiled(PmGeom g, const float* __
         }
     }
     __syncthreads();
-
     // flush: one 16-byte vector reduction per non-zero group of 4 cells
     constexpr int QX = Win::WX / 4;
     for (int i = t; i < Win::CELLS / 4; i += 256) {
@@ -265,99 +300,128 @@ __global__ void __launch_bounds__(256) k_deposit_tiled(PmGeom g, const float* __
     }
 }
 
-// sum over taps of g_c at the particle, c = 0..2, meshes at f, f + M, f + 2M
-template <int ORDER>
-__device__ __forceinline__ void gather3(const float* __restrict__ f, long long M, int log2ng, const AxisTaps& ax,
-                                        const AxisTaps& ay, const AxisTaps& az, float acc[3]) {
-    const int ng = 1 << log2ng, msk = ng - 1;
-#pragma unroll
-    for (int c = 0; c < ORDER; ++c) {
-        const long long zo = (long long)((az.c + c) & msk) * ng;
-#pragma unroll
-        for (int b = 0; b < ORDER; ++b) {
-            const long long yo = (zo + ((ay.c + b) & msk)) * ng;
-            const float wzy = az.w[c] * ay.w[b];
-#pragma unroll
-            for (int a = 0; a < ORDER; ++a) {
-                const long long j = yo + ((ax.c + a) & msk);
-                const float w = wzy * ax.w[a];
-                acc[0] += w * __ldg(&f[j]);
-                acc[1] += w * __ldg(&f[M + j]);
-                acc[2] += w * __ldg(&f[2 * M + j]);
-            }
-        }
-    }
-}
-
-// same from an interleaved float4 mesh (gx, gy, gz, 0): one 16-byte load per tap
-template <int ORDER>
-__device__ __forceinline__ void gather3v(const float4* __restrict__ f, int log2ng, const AxisTaps& ax,
-                                         const AxisTaps& ay, const AxisTaps& az, float acc[3]) {
-    const int ng = 1 << log2ng, msk = ng - 1;
-#pragma unroll
-    for (int c = 0; c < ORDER; ++c) {
-        const long long zo = (long long)((az.c + c) & msk) * ng;
-#pragma unroll
-        for (int b = 0; b < ORDER; ++b) {
-            const long long yo = (zo + ((ay.c + b) & msk)) * ng;
-            const float wzy = az.w[c] * ay.w[b];
-#pragma unroll
-            for (int a = 0; a < ORDER; ++a) {
-                const float4 v = __ldg(&f[yo + ((ax.c + a) & msk)]);
-                const float w = wzy * ax.w[a];
-                acc[0] += w * v.x;
-                acc[1] += w * v.y;
-                acc[2] += w * v.z;
-            }
-        }
-    }
-}
-
-// interpolation + kick + drift_2 from interleaved float4 force meshes [slot][grid][M]
-template <int ORDER, int IL>
-__global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict__ disp, float* __restrict__ vel,
-                                                     const SlotCoef* __restrict__ coef, int cstride,
-                                                     const float4* __restrict__ force4) {
+template <int ORDER, int R>
+__global__ void __launch_bounds__(256) k_deposit_tiled(PmGeom g, const float* __restrict__ disp,
+                                                       const float* __restrict__ vel,
+                                                       const SlotCoef* __restrict__ coef, int cstride, float shift,
+                                                       float* __restrict__ rho) {
+    constexpr int PPT = TileGeom<R>::PPT;
+    extern __shared__ unsigned win[];
+    __shared__ float red[3][8];
     const int slot = blockIdx.y;
     const SlotCoef cf = coef[slot * cstride];
     if (!cf.active) return;
+    const int np = 1 << g.log2np;
+    const TileGeom<R> T(blockIdx.x, np);
     const long long N = 1ll << (3 * g.log2np);
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const Lattice L = lattice_index(i, g.log2np);
+    const float* d = disp + slot * g.slot_part;
+    const float* v = vel ? vel + slot * g.slot_part : nullptr;
+    // pass 1: drifted displacements in cells and their sums
+    float sx[PPT], sy[PPT], sz[PPT];
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const long long i = T.index(p, np);
+        float a = d[i], b = d[N + i], c = d[2 * N + i];
+        if (v) {
+            a += cf.tau1 * v[i];
+            b += cf.tau1 * v[N + i];
+            c += cf.tau1 * v[2 * N + i];
+        }
+        sx[p] = a * g.inv_h + shift;
+        sy[p] = b * g.inv_h + shift;
+        sz[p] = c * g.inv_h + shift;
+        m0 += sx[p];
+        m1 += sy[p];
+        m2 += sz[p];
+    }
+    tile_window_deposit<ORDER, R>(g, T, sx, sy, sz, m0, m1, m2, win, red, rho + slot * g.slot_mesh);
+}
+
+// interpolation + kick + drift_2 from interleaved float4 force meshes [slot][grid][M].
+// Each thread handles IK_PPT particles 256 apart, so that the state loads and the
+// gathers of several particles are in flight at once (the kernel is bound by the
+// latency of its dependent loads: state -> cell -> force taps).
+// Inside a multi-step run the positions between steps can be carried already
+// drifted by the next step's tau1 (so the next deposit reads positions only):
+// predrift_in = the input disp already holds X_half - q; coef_next != NULL = write
+// X_half' - q = X + (tau2 + tau1') V' instead of X' - q.
+constexpr int IK_PPT = 2;
+
+template <int ORDER, int IL>
+__global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict__ disp, float* __restrict__ vel,
+                                                     const SlotCoef* __restrict__ coef, int cstride,
+                                                     const float4* __restrict__ force4, int predrift_in,
+                                                     const SlotCoef* __restrict__ coef_next) {
+    const int slot = blockIdx.y;
+    const SlotCoef cf = coef[slot * cstride];
+    if (!cf.active) return;
+    const float tin = predrift_in ? 0.f : cf.tau1;
+    const float tout = cf.tau2 + (coef_next ? coef_next[slot * cstride].tau1 : 0.f);
+    const long long N = 1ll << (3 * g.log2np);
+    const long long i0 = (long long)blockIdx.x * (256 * IK_PPT) + threadIdx.x;
     float* d = disp + slot * g.slot_part;
     float* v = vel + slot * g.slot_part;
-    float p[3], u[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        u[c] = v[c * N + i];
-        p[c] = d[c * N + i] + cf.tau1 * u[c];          // drift_1: X_half
-    }
     const int ds = g.log2ng - g.log2np;
     const long long M = 1ll << (3 * g.log2ng);
     const float4* f = force4 + slot * g.slot_mesh;
-    float acc[3] = {0.f, 0.f, 0.f};
-    {
-        const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[0] * g.inv_h);
-        const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[1] * g.inv_h);
-        const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[2] * g.inv_h);
-        gather3v<ORDER>(f, g.log2ng, ax, ay, az, acc);
-    }
-    if (IL) {
-        // second grid shifted by half a cell; average the two interpolants
-        float acc1[3] = {0.f, 0.f, 0.f};
-        const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[0] * g.inv_h + 0.5f);
-        const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[1] * g.inv_h + 0.5f);
-        const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[2] * g.inv_h + 0.5f);
-        gather3v<ORDER>(f + M, g.log2ng, ax, ay, az, acc1);
+    float p[IK_PPT][3], u[IK_PPT][3], acc[IK_PPT][3];
+    if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] = 0.5f * (acc[c] + acc1[c]);
+        for (int k = 0; k < IK_PPT; ++k) {
+            const long long ip = i0 + 256 * k + STATE_PREFETCH;
+            if (ip < N) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    prefetch_l2(&d[c * N + ip]);
+                    prefetch_l2(&v[c * N + ip]);
+                }
+            }
+        }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float vn = cf.alpha * u[c] + cf.kick * acc[c];   // kick
-        v[c * N + i] = vn;
-        d[c * N + i] = p[c] + cf.tau2 * vn;                     // drift_2
+    for (int k = 0; k < IK_PPT; ++k) {
+        const long long i = i0 + 256 * k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            // the state is touched once per step: stream it past the caches the gathers use
+            u[k][c] = i < N ? __ldcs(&v[c * N + i]) : 0.f;
+            p[k][c] = (i < N ? __ldcs(&d[c * N + i]) : 0.f) + tin * u[k][c];   // drift_1: X_half
+            acc[k][c] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < IK_PPT; ++k) {
+        const long long i = i0 + 256 * k;
+        if (i >= N) continue;
+        const Lattice L = lattice_index(i, g.log2np);
+        {
+            const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[k][0] * g.inv_h);
+            const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[k][1] * g.inv_h);
+            const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[k][2] * g.inv_h);
+            gather3v<ORDER>(f, g.log2ng, ax, ay, az, acc[k]);
+        }
+        if (IL) {
+            // second grid shifted by half a cell; average the two interpolants
+            float acc1[3] = {0.f, 0.f, 0.f};
+            const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[k][0] * g.inv_h + 0.5f);
+            const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[k][1] * g.inv_h + 0.5f);
+            const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[k][2] * g.inv_h + 0.5f);
+            gather3v<ORDER>(f + M, g.log2ng, ax, ay, az, acc1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[k][c] = 0.5f * (acc[k][c] + acc1[c]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < IK_PPT; ++k) {
+        const long long i = i0 + 256 * k;
+        if (i >= N) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float vn = cf.alpha * u[k][c] + cf.kick * acc[k][c];   // kick
+            __stcs(&v[c * N + i], vn);
+            __stcs(&d[c * N + i], p[k][c] + tout * vn);                   // drift_2 (+ next drift_1)
+        }
     }
 }
 
@@ -651,10 +715,11 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
 }
 
 int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float* vel, const SlotCoef* coef,
-                   int coef_stride, const float4* force4, int nslots, cudaStream_t st) {
+                   int coef_stride, const float4* force4, int nslots, cudaStream_t st, int predrift_in,
+                   const SlotCoef* coef_next) {
     const long long N = 1ll << (3 * g.log2np);
-    dim3 grid((unsigned)((N + 255) / 256), nslots);
-#define PM_IK(O, I) k_interp_kick<O, I><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, force4)
+    dim3 grid((unsigned)((N + 256 * IK_PPT - 1) / (256 * IK_PPT)), nslots);
+#define PM_IK(O, I) k_interp_kick<O, I><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, force4, predrift_in, coef_next)
     if (order == 2 && !interlace) PM_IK(2, 0);
     else if (order == 2 && interlace) PM_IK(2, 1);
     else if (order == 3 && !interlace) PM_IK(3, 0);

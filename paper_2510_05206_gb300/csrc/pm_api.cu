@@ -13,7 +13,7 @@
 #include "cosmo_host.h"
 #include "pm_kernels.h"
 
-#define PM_NPHASE 10
+#define PM_NPHASE 12
 
 namespace {
 
@@ -592,11 +592,40 @@ int pm_step(pm_handle* h, float* disp, float* vel, int32_t step) {
 
 int pm_run(pm_handle* h, float* disp, float* vel, int32_t b, int32_t e) {
     if (!h) return PM_ERR_ARG;
+    if (!disp || !vel) return h->fail(PM_ERR_ARG, "pm_run: NULL buffer");
     if (b < 0 || e < b || e > (int)h->table.size())
         return h->fail(PM_ERR_ARG, "pm_run: bad step range [%d, %d)", b, e);
+    if (e == b) return PM_OK;
+    // Between the steps of a run the positions are carried already drifted by
+    // the next step's tau1 (X_half - q), so each later deposit reads positions only.
+    const bool predrift = h->ngrids == 1 && e - b >= 2;
+    if (!predrift) {
+        for (int s = b; s < e; ++s) {
+            int rc = pm_step(h, disp, vel, s);
+            if (rc) return rc;
+        }
+        return PM_OK;
+    }
+    cudaStream_t st = h->stream;
+    const long long Mg = h->Mg();
+    const PmGeom gd = geom(h, h->ng, h->rho_slot());
+    const PmGeom gf = geom(h, h->ng, Mg);
     for (int s = b; s < e; ++s) {
-        int rc = pm_step(h, disp, vel, s);
+        if (cudaMemsetAsync(h->rho, 0, sizeof(float) * h->rho_slot() * h->B, st) != cudaSuccess)
+            return h->fail(PM_ERR_CUDA, "memset density");
+        h->phase(0, 1);
+        if (s == b)
+            pm_deposit(h->cfg.order, gd, disp, vel, h->d_table + s, 0, 0.f, h->rho, h->B, st);
+        else
+            pm_deposit(h->cfg.order, gd, disp, nullptr, h->d_unit, 0, 0.f, h->rho, h->B, st);
+        h->phase_end();
+        int rc = spectral_force(h, h->rho, h->rho_slot(), Mg, (float)(1.0 / (double)h->Np()), nullptr, h->force, h->B);
         if (rc) return rc;
+        h->phase(6, 1);
+        pm_interp_kick(h->cfg.order, 0, gf, disp, vel, h->d_table + s, 0, h->force, h->B, st, s > b,
+                       s + 1 < e ? h->d_table + s + 1 : nullptr);
+        h->phase_end();
+        if ((rc = h->check_launch("pm_run step"))) return rc;
     }
     return PM_OK;
 }

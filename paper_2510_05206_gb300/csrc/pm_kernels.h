@@ -48,8 +48,10 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
 // A = gather(g) / D_half^2 at X_half = q + disp + tau1 vel; V' = alpha V + kick A; disp' = disp + tau1 V + tau2 V'.
 // force4: [slot][1 or 2 grids][M] float4 (gx, gy, gz, 0); the second grid is shifted by +1/2 cell.
 // g.slot_mesh counts float4 per slot here.
+// predrift_in: disp already holds X_half - q; coef_next (may be NULL): write X + (tau2 + tau1') V'.
 int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float* vel, const SlotCoef* coef,
-                   int coef_stride, const float4* force4, int nslots, cudaStream_t st);
+                   int coef_stride, const float4* force4, int nslots, cudaStream_t st, int predrift_in = 0,
+                   const SlotCoef* coef_next = nullptr);
 // acc[b][c][i] = sum_j g_c,j W(r_j - X_i) at X = q + disp (no kick): stage-level interpolation.
 int pm_interp(int order, int interlace, const PmGeom& g, const float* disp, const float* force, float* acc,
               int nslots, cudaStream_t st);

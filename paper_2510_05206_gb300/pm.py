@@ -211,18 +211,19 @@ class PM:
         return out
 
     PHASES = ("deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv",
-              "interp_kick_drift", "ic_zeldovich", "power_spectrum", "adjoint_spectral")
+              "interp_kick_drift", "ic_zeldovich", "power_spectrum", "adjoint_spectral", "interp_deposit",
+              "reserved")
 
     def profile(self, enable=True):
         self._check(self.lib.pm_profile(self.h, int(bool(enable))))
 
     def profile_read(self):
-        ms = np.zeros(10)
-        calls = np.zeros(10, dtype=np.int64)
-        launches = np.zeros(10, dtype=np.int64)
+        ms = np.zeros(12)
+        calls = np.zeros(12, dtype=np.int64)
+        launches = np.zeros(12, dtype=np.int64)
         self._check(self.lib.pm_profile_read(self.h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                              calls.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                             launches.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 10))
+                                             launches.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 12))
         return {p: dict(ms=ms[i], calls=int(calls[i]), launches=int(launches[i])) for i, p in enumerate(self.PHASES)}
 
     def simulate_host(self, noise, disp=None, vel=None):

@@ -1,0 +1,110 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+* 512^3 particles / 512^3 mesh, L = 1000 Mpc/h, CIC (the bench workload): the
+  Zel'dovich ICs and one full PM step against the FP64 oracle on the whole
+  field (numpy FFTs at 512^3 take ~a minute on the host), plus mass
+  conservation of the 512^3 deposit.
+* 128^3 particles on a 256^3 mesh, L = 250, TSC + interlacing: two steps
+  against the oracle.
+* 128^3 / 128^3, L = 500, 10 steps (adjoint workload): adjoint gradient of the
+  chi^2 density loss against central differences of the GPU forward model on
+  64 random directions.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cosmology, mesh, nbody
+from paper_2510_05206_gb300 import PM, Config, autodiff, inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _rms(a):
+    return np.sqrt(np.mean(np.sum(a ** 2, axis=0)))
+
+
+@pytest.mark.slow
+def test_bench_workload_ic_and_first_step_512():
+    n, L = 512, 1000.0
+    cfg = Config(n_part=n, n_mesh=n, box=L, n_steps=6)
+    pm = PM(cfg, device=DEV)
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal(n ** 3, dtype=np.float32)          # the bench's noise recipe
+    noise = torch.from_numpy(w.reshape(1, -1)).to(DEV)
+    disp, vel = pm.ic_zeldovich(noise)
+    # deposit of the ICs at full size: sum delta = 0 (mass conservation)
+    delta = pm.density(disp)
+    assert abs(float(delta.double().sum())) < 1e-6 * n ** 3
+    del delta
+    ocfg = nbody.Config(n_part=n, n_mesh=n, box=L, n_steps=6)
+    P0, V0 = nbody.zeldovich_ic(ocfg, w.reshape(n, n, n).astype(np.float64))
+    g0 = disp[0].double().cpu().numpy()
+    assert np.max(np.abs(g0 - P0)) / _rms(P0) < 2e-5
+    del g0
+    pm.step(disp, vel, 0)
+    tab = cosmology.step_table(ocfg.get_growth(), 0.02, 1.0, 6)
+    P1, V1 = nbody.step(ocfg, P0, V0, tab[0], nbody.lattice(n, L))
+    g1 = disp[0].double().cpu().numpy()
+    assert np.max(np.abs(g1 - P1)) / _rms(P1) < 1e-4
+    gv = vel[0].double().cpu().numpy()
+    assert np.max(np.abs(gv - V1)) / _rms(V1) < 1e-4
+    pm.close()
+
+
+@pytest.mark.slow
+def test_scaleup_config_tsc_interlaced_two_steps():
+    n, ng, L = 128, 256, 250.0
+    kw = dict(n_part=n, n_mesh=ng, box=L, order=3, n_steps=10)
+    pm = PM(Config(interlace=1, **kw), device=DEV)
+    w = inputs.white_noise(n, seed=2)
+    disp, vel = pm.ic_zeldovich(torch.tensor(w.reshape(1, -1), dtype=torch.float32, device=DEV))
+    pm.run(disp, vel, 0, 2)
+    ocfg = nbody.Config(interlace=True, **kw)
+    P0, V0 = nbody.zeldovich_ic(ocfg, w)
+    P, V = nbody.run(ocfg, P0, V0, n_steps=2)
+    g = disp[0].double().cpu().numpy()
+    assert np.max(np.abs(g - P)) / _rms(P) < 1e-4
+    pm.close()
+
+
+def test_adjoint_workload_central_differences_64_directions():
+    n, L, sigma = 128, 500.0, 0.1
+    pm = PM(Config(n_part=n, n_mesh=n, box=L, n_steps=10), device=DEV)
+    w = inputs.white_noise(n, seed=4)
+    # target: the final density of another realisation plus N(0, sigma^2) noise per cell
+    d_other, v_other = pm.ic_zeldovich(torch.tensor(inputs.white_noise(n, seed=5).reshape(1, -1),
+                                                    dtype=torch.float32, device=DEV))
+    pm.run(d_other, v_other)
+    target = pm.density(d_other).double() + sigma * torch.tensor(
+        inputs.random_field(n, seed=6)[None], dtype=torch.float64, device=DEV)
+    noise = torch.tensor(w.reshape(1, -1), dtype=torch.float32, device=DEV).requires_grad_(True)
+    disp, _ = autodiff.simulate(pm, noise)
+    loss = 0.5 * (((autodiff.density(pm, disp).double() - target) / sigma) ** 2).sum()
+    loss.backward()
+    grad = noise.grad[0].double().cpu().numpy()
+
+    def f(wv):
+        d, v = pm.ic_zeldovich(torch.tensor(wv.reshape(1, -1), dtype=torch.float32, device=DEV))
+        pm.run(d, v)
+        return float(0.5 * (((pm.density(d).double() - target) / sigma) ** 2).sum())
+
+    rng = np.random.default_rng(7)
+    adj, fds = [], []
+    wf = w.reshape(-1)
+    for _ in range(64):
+        e = rng.normal(size=wf.size)
+        e /= np.linalg.norm(e)
+        eps = 1e-2 * np.linalg.norm(wf)
+        fds.append((f(wf + eps * e) - f(wf - eps * e)) / (2 * eps))
+        adj.append(np.dot(grad.reshape(-1), e))
+    adj, fds = np.array(adj), np.array(fds)
+    # a random direction is nearly orthogonal to the gradient, so the per-direction
+    # relative error is ill-conditioned; measure each error against the rms
+    # directional derivative instead (float32 forward model, CIC)
+    err = np.abs(adj - fds) / np.sqrt(np.mean(fds ** 2))
+    assert np.median(err) < 2e-2, np.sort(err)
+    assert np.max(err) < 1e-1, np.sort(err)
+    assert np.corrcoef(adj, fds)[0, 1] > 0.99
+    pm.close()
