@@ -112,9 +112,12 @@ def algorithmic_bytes(n_part, n_mesh):
         "deposit": 14 * N + 4 * M,
         "fft_x_fwd": 4 * M + 4 * M,              # read real mesh, write half spectrum
         "fft_y_fwd": 8 * M,                      # read + write half spectrum
-        "fft_z_green": 4 * M + 12 * M,           # read 1 spectrum, write 3
-        "fft_y_inv": 3 * 8 * M,                  # 3 spectra in place
-        "fft_x_inv": 12 * M + 12 * M,            # 3 spectra -> 3 force components (stored as float4: padding not counted)
+        # finite-difference gradient (grad_order 2/4/6): the z pass maps the density
+        # spectrum to the potential's, one inverse transform, then the stencil
+        "fft_z_green": 4 * M + 4 * M,            # read 1 spectrum, write 1
+        "fft_y_inv": 8 * M,                      # 1 spectrum in place
+        "fft_x_inv": 4 * M + 4 * M,              # potential spectrum -> real potential
+        "grad_stencil": 4 * M + 12 * M,          # read phi, write 3 components (float4 padding not counted)
         "interp_kick_drift": 48 * N + 12 * M,    # read disp, vel, 3 force components; write disp, vel
     }
 

@@ -186,8 +186,8 @@ int pm_density_vjp(pm_handle* h, const float* disp, int32_t n_mesh, int32_t orde
  * 0 deposit, 1 forward x FFT, 2 forward y FFT, 3 z FFT with the Fourier-space
  * operator, 4 inverse y FFT, 5 inverse x FFT, 6 interpolation + kick + drift,
  * 7 Zel'dovich ICs, 8 P(k), 9 adjoint spectral passes, 10 interpolation + kick + drift
- * fused with the next step's deposit (pm_run), 11 reserved.  Kernel launches are
- * counted always. */
+ * fused with the next step's deposit (reserved), 11 real-space gradient stencil.
+ * Kernel launches are counted always. */
 int pm_profile(pm_handle* h, int32_t enable);
 
 /* Synchronises the stream and returns, per phase (cap >= 12 entries), the summed

@@ -193,7 +193,7 @@ struct ZArgs {
     float kf;                 // 2 pi / L
 };
 
-enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5 };
+enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5, Z_POT = 6, Z_POT_IL = 7 };
 
 template <int LOG2N, int MODE>
 __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZArgs a) {
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
     const ColTile A2{sm + 2 * n + 2 * TE};
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         tw[i] = a.tw[i];
-        if (MODE == Z_FORCE || MODE == Z_FORCE_IL || MODE == Z_ADJ) {
+        if (MODE == Z_FORCE || MODE == Z_FORCE_IL || MODE == Z_ADJ || MODE == Z_POT || MODE == Z_POT_IL) {
             lap[i] = a.lap1[i];
             grad[i] = a.grad1[i];
         }
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
     }
 
     fft_io<n, COL_TILE, -1, false, true>(in0, A, A, tw, 1);
-    if (MODE == Z_FORCE_IL) {
+    if (MODE == Z_FORCE_IL || MODE == Z_POT_IL) {
         __syncthreads();
         fft_io<n, COL_TILE, -1, false, true>(GCols{const_cast<float2*>(a.in[1]) + off, ES}, A2, A2, tw, 1);
     }
@@ -296,6 +296,34 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
         double* dst = a.pk_out + (long long)slot * a.nbins;
         for (int i = threadIdx.x; i < a.nbins; i += blockDim.x)
             if (acc[i] != 0.0) atomicAdd(&dst[i], acc[i]);
+        return;
+    }
+
+    if (MODE == Z_POT || MODE == Z_POT_IL) {
+        // potential phi^ = scale * delta^ / K_lap(k) (k = 0 -> 0); the gradient of a
+        // finite-difference order is applied afterwards as a real-space stencil.
+        // Interlaced: delta^ = (d0^ + exp(i k.s) d1^)/2 and phi^ on both grids (phi^ and
+        // phi^ exp(-i k.s)), every Nyquist plane zeroed.
+        const int ngrid = MODE == Z_POT_IL ? 2 : 1;
+        for (int gi = 0; gi < ngrid; ++gi) {
+            auto mult = [&](int l, int e) -> float2 {
+                const int kx = kx0 + l;
+                float2 r = make_float2(0.f, 0.f);
+                if (kx > n / 2 || (kx | y | e) == 0) return r;
+                float2 d = A(l, e);
+                if (MODE == Z_POT_IL) {
+                    if (kx == n / 2 || y == n / 2 || e == n / 2) return r;
+                    const int mz = freq_index(e, n);
+                    float sn, cs;
+                    sincospif((float)(kx + my + mz) / n, &sn, &cs);
+                    d = cscale(cadd(d, cmul(make_float2(cs, sn), A2(l, e))), 0.5f);
+                    if (gi == 1) d = cmul(d, make_float2(cs, -sn));
+                }
+                return cscale(d, a.scale / (lap[kx] + lap[y] + lap[e]));
+            };
+            fft_io<n, COL_TILE, 1, false, false>(mult, GCols{a.out[gi] + off, ES}, B, tw, 1);
+            __syncthreads();
+        }
         return;
     }
 
@@ -405,7 +433,7 @@ void launch_y(float2* data, long long stride, int nmesh, int dir, const float2* 
 template <int LOG2N, int MODE>
 void launch_z_mode(const ZArgs& a, int nslots, cudaStream_t st) {
     constexpr int n = 1 << LOG2N;
-    const int ntile = (MODE == Z_FORCE_IL || MODE == Z_ADJ || MODE == Z_IC_ADJ) ? 3 : 2;
+    const int ntile = (MODE == Z_FORCE_IL || MODE == Z_ADJ || MODE == Z_IC_ADJ || MODE == Z_POT_IL) ? 3 : 2;
     const size_t smem = (size_t)(ntile * col_tile_elems(n) + 2 * n) * sizeof(float2);
     dim3 grid(n / 2 / COL_TILE + 1, n, nslots);
     set_smem(k_fft_z<LOG2N, MODE>, smem);
@@ -421,6 +449,8 @@ void launch_z(int mode, const ZArgs& a, int nslots, cudaStream_t st) {
         case Z_PK: launch_z_mode<LOG2N, Z_PK>(a, nslots, st); break;
         case Z_ADJ: launch_z_mode<LOG2N, Z_ADJ>(a, nslots, st); break;
         case Z_IC_ADJ: launch_z_mode<LOG2N, Z_IC_ADJ>(a, nslots, st); break;
+        case Z_POT: launch_z_mode<LOG2N, Z_POT>(a, nslots, st); break;
+        case Z_POT_IL: launch_z_mode<LOG2N, Z_POT_IL>(a, nslots, st); break;
     }
 }
 

@@ -484,6 +484,41 @@ __global__ void __launch_bounds__(256) k_interp(PmGeom g, float* __restrict__ di
     }
 }
 
+// ------------------------------------------------------------------ gradient stencil
+// g = -D1 phi with the finite-difference gradients of Table 2 applied in real
+// space: order 2: 1/2 [-1 0 1]; order 4: 1/12 [1 -8 0 8 -1]; order 6:
+// 1/60 [-1 9 -45 0 45 -9 1] (times 1/H).  Their Fourier transforms are the
+// gradient kernels used in k-space, so this equals applying them there, with
+// one inverse FFT (of the potential) instead of three.
+template <int GO>
+__global__ void __launch_bounds__(256) k_grad_stencil(int log2n, float inv_h, const float* __restrict__ phi,
+                                                      long long phi_stride, float4* __restrict__ out,
+                                                      long long f_stride) {
+    constexpr int R = GO / 2;
+    const float c1 = GO == 2 ? 0.5f : (GO == 4 ? 8.f / 12.f : 45.f / 60.f);
+    const float c2 = GO == 4 ? -1.f / 12.f : -9.f / 60.f;
+    const float c3 = 1.f / 60.f;
+    const int n = 1 << log2n, msk = n - 1;
+    const long long M = 1ll << (3 * log2n);
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const float* f = phi + blockIdx.y * phi_stride;
+    const int x = (int)(j & msk), y = (int)((j >> log2n) & msk), z = (int)(j >> (2 * log2n));
+    auto at = [&](int xx, int yy, int zz) -> float {
+        return __ldg(&f[((long long)(zz & msk) << (2 * log2n)) + ((long long)(yy & msk) << log2n) + (xx & msk)]);
+    };
+    float g[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int dx = c == 0, dy = c == 1, dz = c == 2;
+        float d = c1 * (at(x + dx, y + dy, z + dz) - at(x - dx, y - dy, z - dz));
+        if (R >= 2) d += c2 * (at(x + 2 * dx, y + 2 * dy, z + 2 * dz) - at(x - 2 * dx, y - 2 * dy, z - 2 * dz));
+        if (R >= 3) d += c3 * (at(x + 3 * dx, y + 3 * dy, z + 3 * dz) - at(x - 3 * dx, y - 3 * dy, z - 3 * dz));
+        g[c] = -d * inv_h;
+    }
+    out[blockIdx.y * f_stride + j] = make_float4(g[0], g[1], g[2], 0.f);
+}
+
 // ------------------------------------------------------------------ adjoint
 // Backward-in-time DKD (Sec. 2.7, Table 5) with the App. C pullbacks of the
 // scatter (deposit) and gather (interpolation).  g = G rho with
@@ -787,5 +822,16 @@ int pm_dot(const float* a, const float* b, long long n, double* out, int nslots,
 
 int pm_axpby(float* out, const float* x, const float* y, float a, float b, long long n, cudaStream_t st) {
     k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, x, y, a, b, n);
+    return 0;
+}
+
+int pm_grad_stencil(int grad_order, int log2n, float inv_h, const float* phi, long long phi_stride, float4* force4,
+                    long long f_stride, int nmesh, cudaStream_t st) {
+    const long long M = 1ll << (3 * log2n);
+    dim3 grid((unsigned)((M + 255) / 256), nmesh);
+    if (grad_order == 2) k_grad_stencil<2><<<grid, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
+    else if (grad_order == 4) k_grad_stencil<4><<<grid, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
+    else if (grad_order == 6) k_grad_stencil<6><<<grid, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
+    else return -1;
     return 0;
 }

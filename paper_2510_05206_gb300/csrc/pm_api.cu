@@ -252,13 +252,37 @@ int spectral_force(pm_handle* h, const float* src, long long src_slot, long long
     PmZPass z{};
     z.in[0] = h->spec;
     z.in[1] = h->spec + S;
-    for (int c = 0; c < h->ncomp; ++c) z.out[c] = h->spec + c * S;
     z.slot_stride = SS;
     z.tw = h->d_tw[l2];
     z.lap1 = h->d_lap;
     z.grad1 = h->d_grad;
     z.scale = scale;
     z.kf = (float)(2.0 * M_PI / h->cfg.box);
+    const int go = h->cfg.grad_order;
+    if (force4 && go != 0) {
+        // finite-difference gradient: one potential per grid, inverse transformed once,
+        // then g = -D1 phi as a real-space stencil (the same operator as D1(k) in k space)
+        for (int g = 0; g < h->ngrids; ++g) z.out[g] = h->spec + g * S;
+        h->phase(3, 1);
+        pm_fft_z(l2, h->ngrids == 2 ? PM_Z_POT_IL : PM_Z_POT, z, nslots, st);
+        h->phase_end();
+        h->phase(4, h->ngrids);
+        for (int g = 0; g < h->ngrids; ++g) pm_fft_y(l2, h->spec + g * S, SS, nslots, 1, h->d_tw[l2], st);
+        h->phase_end();
+        // the potential overwrites the density (already transformed)
+        h->phase(5, h->ngrids);
+        for (int g = 0; g < h->ngrids; ++g)
+            pm_fft_c2r_x(l2, h->spec + g * S, SS, h->rho + g * h->Mg(), h->rho_slot(), nullptr, 0, 0.f, nslots,
+                         h->d_tw[l2], st);
+        h->phase_end();
+        h->phase(11, h->ngrids);
+        for (int g = 0; g < h->ngrids; ++g)
+            pm_grad_stencil(go, l2, (float)(n / h->cfg.box), h->rho + g * h->Mg(), h->rho_slot(), force4 + g * h->Mg(),
+                            (long long)h->ngrids * h->Mg(), nslots, st);
+        h->phase_end();
+        return h->check_launch("force spectral passes");
+    }
+    for (int c = 0; c < h->ncomp; ++c) z.out[c] = h->spec + c * S;
     h->phase(3, 1);
     pm_fft_z(l2, h->force_mode(), z, nslots, st);
     h->phase_end();

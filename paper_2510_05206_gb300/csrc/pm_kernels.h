@@ -20,7 +20,8 @@ struct PmZPass {
     float kf;
 };
 
-enum { PM_Z_FORCE = 0, PM_Z_FORCE_IL = 1, PM_Z_IC = 2, PM_Z_PK = 3, PM_Z_ADJ = 4, PM_Z_IC_ADJ = 5 };
+enum { PM_Z_FORCE = 0, PM_Z_FORCE_IL = 1, PM_Z_IC = 2, PM_Z_PK = 3, PM_Z_ADJ = 4, PM_Z_IC_ADJ = 5, PM_Z_POT = 6,
+       PM_Z_POT_IL = 7 };
 
 int pm_fft_r2c_x(int log2n, const float* in, long long in_stride, float2* out, long long out_stride, int nmesh,
                  const float2* tw, cudaStream_t st);
@@ -32,6 +33,12 @@ int pm_fft_c2r_x3(int log2n, const float2* in, long long comp_stride, long long 
                   long long out_stride, int nmesh, const float2* tw, cudaStream_t st);
 int pm_fft_y(int log2n, float2* data, long long stride, int nmesh, int dir, const float2* tw, cudaStream_t st);
 int pm_fft_z(int log2n, int mode, const PmZPass& p, int nslots, cudaStream_t st);
+
+// force4[q][j] = (-D1_x phi, -D1_y phi, -D1_z phi, 0) at every cell of the n^3 mesh
+// phi[q] (q < nmesh; phi slot stride phi_stride floats, force4 stride f_stride float4),
+// D1 the finite-difference gradient of Table 2 of order 2, 4 or 6 (cell size 1/inv_h).
+int pm_grad_stencil(int grad_order, int log2n, float inv_h, const float* phi, long long phi_stride, float4* force4,
+                    long long f_stride, int nmesh, cudaStream_t st);
 
 // Particle kernels.  Geometry shared by deposit and interpolation.
 struct PmGeom {

@@ -211,8 +211,8 @@ class PM:
         return out
 
     PHASES = ("deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv",
-              "interp_kick_drift", "ic_zeldovich", "power_spectrum", "adjoint_spectral", "interp_deposit",
-              "reserved")
+              "interp_kick_drift", "ic_zeldovich", "power_spectrum", "adjoint_spectral", "reserved",
+              "grad_stencil")
 
     def profile(self, enable=True):
         self._check(self.lib.pm_profile(self.h, int(bool(enable))))

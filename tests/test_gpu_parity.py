@@ -125,6 +125,9 @@ def test_full_run_config1_parity():
     dict(n_part=32, n_mesh=64, box=125.0, order=3, interlace=1, n_steps=10),      # config-2 settings, reduced
     dict(n_part=32, n_mesh=32, box=200.0, order=3, n_steps=4, stepper=1),         # FastPM
     dict(n_part=16, n_mesh=32, box=100.0, order=2, n_steps=5, time_var=1, grad_order=2, lap_order=2),
+    dict(n_part=32, n_mesh=32, box=256.0, order=2, n_steps=3, grad_order=0),                # exact i k gradient
+    dict(n_part=32, n_mesh=64, box=200.0, order=2, n_steps=3, grad_order=6, lap_order=4),
+    dict(n_part=32, n_mesh=32, box=150.0, order=2, interlace=1, n_steps=3, grad_order=0),   # 6 inverse FFTs
 ])
 def test_full_run_variants_parity(kw):
     pm, disp, vel, P1, V1 = _run_pair(kw, seed=2)
