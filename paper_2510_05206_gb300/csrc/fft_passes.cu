@@ -263,10 +263,18 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
         // reduced with shuffles, then one shared-memory atomic per bin and warp, then
         // one global atomic per bin and CTA.  Mode counts and mean |k| per bin depend
         // on the mesh only and are tabulated exactly on the host.
-        double* acc = reinterpret_cast<double*>(B.s);   // nbins doubles (<= TE float2)
-        for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) acc[i] = 0.0;
+        // per-warp private FP64 accumulators when they fit (no contention between
+        // warps), else one shared set updated atomically
+        double* acc = reinterpret_cast<double*>(B.s);
+        constexpr int NW = (1 << LOG2N) >= 32 ? (1 << LOG2N) / 32 : 1;
+        // blocks of n < 32 threads are a partial warp: synchronise only its lanes
+        constexpr unsigned FULL = (1 << LOG2N) >= 32 ? 0xffffffffu : ((1u << (1 << LOG2N)) - 1u);
+        const bool priv = NW * a.nbins <= TE;
+        const int nacc = priv ? NW * a.nbins : a.nbins;
+        for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0.0;
         __syncthreads();
         const int lane = threadIdx.x & 31;
+        double* wacc = priv ? acc + (threadIdx.x >> 5) * a.nbins : acc;
         constexpr int T = n * COL_TILE;
         for (int i = threadIdx.x; i < T; i += blockDim.x) {   // T is a multiple of blockDim: no divergence
             const int e = i / COL_TILE, l = i % COL_TILE;
@@ -280,18 +288,29 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
                 v = ((kx == 0 || kx == n / 2) ? 1.f : 2.f) * (d.x * d.x + d.y * d.y);
             }
             // the float sum of at most 32 lanes feeds an FP64 per-bin accumulator
-            unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
+            unsigned todo = __ballot_sync(FULL, b >= 0);
             while (todo) {
                 const int leader = __ffs(todo) - 1;
-                const int bl = __shfl_sync(0xffffffffu, b, leader);
+                const int bl = __shfl_sync(FULL, b, leader);
                 const bool mine = (b == bl);
                 float sv = mine ? v : 0.f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-                if (lane == leader) atomicAdd(&acc[bl], (double)sv);
-                todo &= ~__ballot_sync(0xffffffffu, mine);
+                for (int o = 16; o > 0; o >>= 1)
+                    if (o < (1 << LOG2N)) sv += __shfl_xor_sync(FULL, sv, o);
+                if (lane == leader) {
+                    if (priv) wacc[bl] += (double)sv;
+                    else atomicAdd(&wacc[bl], (double)sv);
+                }
+                todo &= ~__ballot_sync(FULL, mine);
             }
         }
+        __syncthreads();
+        if (priv)
+            for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+                double sum = 0.0;
+                for (int w = 0; w < NW; ++w) sum += acc[w * a.nbins + i];
+                acc[i] = sum;   // each i is owned by one thread: reading row 0 before writing it is safe
+            }
         __syncthreads();
         double* dst = a.pk_out + (long long)slot * a.nbins;
         for (int i = threadIdx.x; i < a.nbins; i += blockDim.x)
