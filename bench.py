@@ -101,6 +101,26 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel's source changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic_pm_512cubed.md")
+    csrc = os.path.join(ROOT, "paper_2510_05206_gb300", "csrc")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        p = ln.split()
+        if len(p) == 5 and p[0] == "TRAFFIC" and p[1] == kernel:
+            data = b"".join(open(os.path.join(csrc, f), "rb").read() for f in p[3].split("+"))
+            if hashlib.sha256(data).hexdigest()[:16] == p[4]:
+                return int(p[2])
+            return None
+    return None
+
+
 def algorithmic_bytes(n_part, n_mesh):
     """Compulsory HBM bytes per launch of each phase (float32; M = mesh cells,
     N = particles; complex half spectra count as M/2 complex = 4M bytes)."""
@@ -317,8 +337,9 @@ def main():
             entry["frac"] = entry["gbs"] / peak
         kernels[name] = entry
     dom = max((k for k in kernels if k in alg), key=lambda k: kernels[k]["share"])
+    traffic = measured_traffic(dom) if (n, cfg.n_mesh) == (512, 512) else None
     roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",
-            "frac": kernels[dom]["frac"], "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+            "frac": kernels[dom]["frac"], "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes_per_launch": alg[dom]}
     launches = sum(p["launches"] for p in prof.values())
 
