@@ -223,6 +223,82 @@ def serving_benchmark(n_req, dev):
     return out
 
 
+def adjoint_benchmark(dev, reps=5):
+    """Gradient of the field-level chi^2 (128^3 particles on a 128^3 mesh,
+    L = 500 Mpc/h, 10 BullFrog steps, CIC, sigma = 0.1 per cell) with respect to
+    the white-noise field and sigma8: ICs + forward run + density, then the
+    density VJP, the reverse adjoint of the 10 steps and the IC adjoint.
+    Reports ms per gradient and the device memory the handle holds for 10 and
+    for 40 steps (the adjoint stores no trajectory)."""
+    import numpy as np
+    import torch
+    from paper_2510_05206_gb300 import PM, Config, workspace_bytes
+    n, L, sigma = 128, 500.0, 0.1
+    cfg = Config(n_part=n, n_mesh=n, box=L, n_steps=10)
+    pm = PM(cfg, device=dev)
+    rng = np.random.default_rng(NOISE_SEED + 4)
+    noise = torch.from_numpy(rng.standard_normal((1, n ** 3), dtype=np.float32)).to(dev)
+    target = torch.from_numpy(rng.standard_normal((1, n, n, n), dtype=np.float32)).to(dev) * sigma
+    disp, vel = pm.new_state()
+    adv = torch.empty_like(vel)
+
+    def grad():
+        pm.ic_zeldovich(noise, disp, vel)
+        pm.run(disp, vel)
+        dd = (pm.density(disp) - target) / sigma ** 2
+        ad = pm.density_vjp(disp, dd)
+        adv.zero_()
+        pm.adjoint(disp, vel, ad, adv)
+        return pm.ic_adjoint(noise, ad, adv)
+
+    for _ in range(3):
+        grad()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        grad()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    pm.close()
+    ws10 = workspace_bytes(cfg)
+    ws40 = workspace_bytes(Config(n_part=n, n_mesh=n, box=L, n_steps=40))
+    return {"workload": "chi2_gradient_128cubed_on_128cubed_L500_10step_cic", "ms_per_gradient": ms,
+            "gradients_per_s": 1e3 / ms, "particle_steps_per_s_fwd_plus_adj": n ** 3 * 10 * 2 / (ms / 1e3),
+            "workspace_bytes_10_steps": ws10, "workspace_bytes_40_steps": ws40, "reps": reps}
+
+
+def scaleup_benchmark(dev, reps=3):
+    """One run of the scale-up configuration: 128^3 particles on a 256^3 mesh
+    (L = 250 Mpc/h), TSC with interlacing, ICs + 10 BullFrog steps."""
+    import numpy as np
+    import torch
+    from paper_2510_05206_gb300 import PM, Config
+    n = 128
+    pm = PM(Config(n_part=n, n_mesh=256, box=250.0, order=3, interlace=1, n_steps=10), device=dev)
+    rng = np.random.default_rng(NOISE_SEED + 2)
+    noise = torch.from_numpy(rng.standard_normal((1, n ** 3), dtype=np.float32)).to(dev)
+    disp, vel = pm.new_state()
+    for _ in range(3):
+        pm.ic_zeldovich(noise, disp, vel)
+        pm.run(disp, vel)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        pm.ic_zeldovich(noise, disp, vel)
+        pm.run(disp, vel)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    pm.close()
+    return {"workload": "pm_128cubed_on_256cubed_L250_tsc_interlaced_10step", "ms_per_run": ms,
+            "ms_per_pm_step": ms / 10, "particle_steps_per_s": n ** 3 * 10 / (ms / 1e3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -235,6 +311,7 @@ def main():
     ap.add_argument("--mesh", type=int, default=0, help="mesh cells per dimension (default = --size)")
     ap.add_argument("--no-serving", action="store_true", help="skip the continuous-batching measurement")
     ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint and scale-up measurements")
     args = ap.parse_args()
     if args.size != 512 or (args.mesh and args.mesh != 512):
         # a reduced case for profiling captures; the config says so
@@ -350,6 +427,9 @@ def main():
             "e2e": e2e,
             "clocks": clock_info,
             "ms_per_pm_step": ms / args.steps / cfg.n_steps}
+    if not args.no_extra:
+        line["adjoint"] = adjoint_benchmark(dev)
+        line["scaleup"] = scaleup_benchmark(dev)
     if not args.no_serving:
         line["serving"] = serving_benchmark(args.serve_requests, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -519,6 +519,39 @@ __global__ void __launch_bounds__(256) k_grad_stencil(int log2n, float inv_h, co
     out[blockIdx.y * f_stride + j] = make_float4(g[0], g[1], g[2], 0.f);
 }
 
+// div[q][j] = sum_c D1_c s_c at every cell for three planar meshes s_c (q < nmesh,
+// s slot stride s_stride floats, c-th mesh at c * M; div slot stride d_stride).
+// Its transpose pairs with k_grad_stencil: D1 is antisymmetric, so the adjoint
+// of g_c = -D1_c Lap^-1 rho is rho* = Lap^-1 sum_c D1_c g*_c.
+template <int GO>
+__global__ void __launch_bounds__(256) k_div_stencil(int log2n, float inv_h, const float* __restrict__ s3,
+                                                     long long s_stride, float* __restrict__ div,
+                                                     long long d_stride) {
+    constexpr int R = GO / 2;
+    const float c1 = GO == 2 ? 0.5f : (GO == 4 ? 8.f / 12.f : 45.f / 60.f);
+    const float c2 = GO == 4 ? -1.f / 12.f : -9.f / 60.f;
+    const float c3 = 1.f / 60.f;
+    const int n = 1 << log2n, msk = n - 1;
+    const long long M = 1ll << (3 * log2n);
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int x = (int)(j & msk), y = (int)((j >> log2n) & msk), z = (int)(j >> (2 * log2n));
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float* f = s3 + blockIdx.y * s_stride + c * M;
+        auto at = [&](int xx, int yy, int zz) -> float {
+            return __ldg(&f[((long long)(zz & msk) << (2 * log2n)) + ((long long)(yy & msk) << log2n) + (xx & msk)]);
+        };
+        const int dx = c == 0, dy = c == 1, dz = c == 2;
+        float d = c1 * (at(x + dx, y + dy, z + dz) - at(x - dx, y - dy, z - dz));
+        if (R >= 2) d += c2 * (at(x + 2 * dx, y + 2 * dy, z + 2 * dz) - at(x - 2 * dx, y - 2 * dy, z - 2 * dz));
+        if (R >= 3) d += c3 * (at(x + 3 * dx, y + 3 * dy, z + 3 * dz) - at(x - 3 * dx, y - 3 * dy, z - 3 * dz));
+        acc += d * inv_h;
+    }
+    div[blockIdx.y * d_stride + j] = acc;
+}
+
 // ------------------------------------------------------------------ adjoint
 // Backward-in-time DKD (Sec. 2.7, Table 5) with the App. C pullbacks of the
 // scatter (deposit) and gather (interpolation).  g = G rho with
@@ -832,6 +865,17 @@ int pm_grad_stencil(int grad_order, int log2n, float inv_h, const float* phi, lo
     if (grad_order == 2) k_grad_stencil<2><<<grid, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
     else if (grad_order == 4) k_grad_stencil<4><<<grid, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
     else if (grad_order == 6) k_grad_stencil<6><<<grid, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
+    else return -1;
+    return 0;
+}
+
+int pm_div_stencil(int grad_order, int log2n, float inv_h, const float* s3, long long s_stride, float* div,
+                   long long d_stride, int nmesh, cudaStream_t st) {
+    const long long M = 1ll << (3 * log2n);
+    dim3 grid((unsigned)((M + 255) / 256), nmesh);
+    if (grad_order == 2) k_div_stencil<2><<<grid, 256, 0, st>>>(log2n, inv_h, s3, s_stride, div, d_stride);
+    else if (grad_order == 4) k_div_stencil<4><<<grid, 256, 0, st>>>(log2n, inv_h, s3, s_stride, div, d_stride);
+    else if (grad_order == 6) k_div_stencil<6><<<grid, 256, 0, st>>>(log2n, inv_h, s3, s_stride, div, d_stride);
     else return -1;
     return 0;
 }

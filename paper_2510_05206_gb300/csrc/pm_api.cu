@@ -807,19 +807,39 @@ int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adisp, float* avel,
         h->phase_end();
         // rho* = sum_c G_c^T s_c, G_c^T = (1/N) IDFT diag(conj m_c) DFT
         h->phase(9, 5);
-        pm_fft_r2c_x(l2, h->adj3, Mg, h->spec, S, 3 * h->B, h->d_tw[l2], st);
-        pm_fft_y(l2, h->spec, S, 3 * h->B, -1, h->d_tw[l2], st);
-        PmZPass z{};
-        for (int c = 0; c < 3; ++c) z.in[c] = h->spec + c * S;
-        z.out[0] = h->spec;
-        z.slot_stride = 3 * S;
-        z.tw = h->d_tw[l2];
-        z.lap1 = h->d_lap;
-        z.grad1 = h->d_grad;
-        z.scale = (float)(1.0 / (double)h->Np());
-        pm_fft_z(l2, PM_Z_ADJ, z, h->B, st);
-        pm_fft_y(l2, h->spec, 3 * S, h->B, 1, h->d_tw[l2], st);
-        pm_fft_c2r_x(l2, h->spec, 3 * S, h->rho, h->rho_slot(), nullptr, 0, 0.f, h->B, h->d_tw[l2], st);
+        if (h->cfg.grad_order != 0) {
+            // finite-difference gradient: G_c^T s_c summed = Lap^-1 (sum_c D1_c s_c), the divergence
+            // stencil in real space and one potential solve (the z pass of the forward force)
+            pm_div_stencil(h->cfg.grad_order, l2, (float)(n / h->cfg.box), h->adj3, 3 * Mg, h->rho, h->rho_slot(), h->B,
+                           st);
+            pm_fft_r2c_x(l2, h->rho, h->rho_slot(), h->spec, S, h->B, h->d_tw[l2], st);
+            pm_fft_y(l2, h->spec, S, h->B, -1, h->d_tw[l2], st);
+            PmZPass z{};
+            z.in[0] = h->spec;
+            z.out[0] = h->spec;
+            z.slot_stride = S;
+            z.tw = h->d_tw[l2];
+            z.lap1 = h->d_lap;
+            z.grad1 = h->d_grad;
+            z.scale = (float)(1.0 / (double)h->Np());
+            pm_fft_z(l2, PM_Z_POT, z, h->B, st);
+            pm_fft_y(l2, h->spec, S, h->B, 1, h->d_tw[l2], st);
+            pm_fft_c2r_x(l2, h->spec, S, h->rho, h->rho_slot(), nullptr, 0, 0.f, h->B, h->d_tw[l2], st);
+        } else {
+            pm_fft_r2c_x(l2, h->adj3, Mg, h->spec, S, 3 * h->B, h->d_tw[l2], st);
+            pm_fft_y(l2, h->spec, S, 3 * h->B, -1, h->d_tw[l2], st);
+            PmZPass z{};
+            for (int c = 0; c < 3; ++c) z.in[c] = h->spec + c * S;
+            z.out[0] = h->spec;
+            z.slot_stride = 3 * S;
+            z.tw = h->d_tw[l2];
+            z.lap1 = h->d_lap;
+            z.grad1 = h->d_grad;
+            z.scale = (float)(1.0 / (double)h->Np());
+            pm_fft_z(l2, PM_Z_ADJ, z, h->B, st);
+            pm_fft_y(l2, h->spec, 3 * S, h->B, 1, h->d_tw[l2], st);
+            pm_fft_c2r_x(l2, h->spec, 3 * S, h->rho, h->rho_slot(), nullptr, 0, 0.f, h->B, h->d_tw[l2], st);
+        }
         h->phase_end();
         h->phase(6, 1);
         pm_adj_gather_grad(order, 1, gd, disp, vel, adisp, avel, coef, 0, h->rho, 0.f, h->B, st);

@@ -40,6 +40,11 @@ int pm_fft_z(int log2n, int mode, const PmZPass& p, int nslots, cudaStream_t st)
 int pm_grad_stencil(int grad_order, int log2n, float inv_h, const float* phi, long long phi_stride, float4* force4,
                     long long f_stride, int nmesh, cudaStream_t st);
 
+// div[q] = sum_c D1_c s_c of three planar meshes per q (c-th at c * n^3), the transpose
+// partner of pm_grad_stencil.
+int pm_div_stencil(int grad_order, int log2n, float inv_h, const float* s3, long long s_stride, float* div,
+                   long long d_stride, int nmesh, cudaStream_t st);
+
 // Particle kernels.  Geometry shared by deposit and interpolation.
 struct PmGeom {
     int log2np;          // particles per dimension = 1 << log2np

@@ -68,6 +68,22 @@ def test_adjoint_gradient_matches_oracle(order):
         assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 2e-3
 
 
+@pytest.mark.parametrize("grad,lap", [(0, 0), (2, 2), (6, 4), (4, 0)])
+def test_adjoint_gradient_kernels_match_oracle(grad, lap):
+    # the transposed force operator for the exact i k gradient (three forward
+    # transforms, conj multipliers) and for the Table 2 finite differences
+    # (divergence stencil, one potential solve)
+    n, L, sigma = 32, 200.0, 0.1
+    kw = dict(n_part=n, n_mesh=n, box=L, order=3, n_steps=3, grad_order=grad, lap_order=lap)
+    pm = PM(Config(**kw), device=DEV)
+    ocfg = nbody.Config(**kw)
+    w = inputs.white_noise(n, seed=36)
+    target = 0.5 * inputs.white_noise(n, seed=37)
+    _, g = _gpu_grad(pm, w, _t(target[None]).double(), sigma)
+    ref, _ = _oracle_grad(ocfg, w, target, sigma)
+    assert np.max(np.abs(g - ref)) / np.max(np.abs(ref)) < 2e-4
+
+
 def test_sigma8_gradient_matches_oracle():
     n, L, sigma = 32, 200.0, 0.1
     cfg, ocfg = _cfgs(n, n, L, 3, 3)
