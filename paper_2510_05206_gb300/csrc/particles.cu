@@ -141,21 +141,29 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 // arrives while the current ones wait on their force gathers
 constexpr long long STATE_PREFETCH = 1ll << 17;
 
-// same from an interleaved float4 mesh (gx, gy, gz, 0): one 16-byte load per tap
+// same from an interleaved float4 mesh (gx, gy, gz, 0): one 16-byte load per tap.
+// Offsets are 32-bit (meshes hold at most 2^30 cells) and the periodic wrap of
+// each axis is taken once per tap line, not per tap.
 template <int ORDER>
 __device__ __forceinline__ void gather3v(const float4* __restrict__ f, int log2ng, const AxisTaps& ax,
                                          const AxisTaps& ay, const AxisTaps& az, float acc[3]) {
-    const int ng = 1 << log2ng, msk = ng - 1;
+    const int msk = (1 << log2ng) - 1;
+    int xo[ORDER], yo[ORDER], zo[ORDER];
+#pragma unroll
+    for (int a = 0; a < ORDER; ++a) {
+        xo[a] = (ax.c + a) & msk;
+        yo[a] = ((ay.c + a) & msk) << log2ng;
+        zo[a] = ((az.c + a) & msk) << (2 * log2ng);
+    }
 #pragma unroll
     for (int c = 0; c < ORDER; ++c) {
-        const long long zo = (long long)((az.c + c) & msk) * ng;
 #pragma unroll
         for (int b = 0; b < ORDER; ++b) {
-            const long long yo = (zo + ((ay.c + b) & msk)) * ng;
+            const int row = zo[c] + yo[b];
             const float wzy = az.w[c] * ay.w[b];
 #pragma unroll
             for (int a = 0; a < ORDER; ++a) {
-                const float4 v = __ldg(&f[yo + ((ax.c + a) & msk)]);
+                const float4 v = __ldg(f + (row + xo[a]));
                 const float w = wzy * ax.w[a];
                 acc[0] += w * v.x;
                 acc[1] += w * v.y;
@@ -166,30 +174,32 @@ __device__ __forceinline__ void gather3v(const float4* __restrict__ f, int log2n
 }
 
 // Lagrangian-tile deposit through a shared-memory window.
-// A CTA owns a tile of (32/R) x (8/R) x (8/R) lattice sites (R = n_mesh / n_part in
-// {1, 2}), i.e. a 32 x 8 x 8 block of cells.  Pass 1 loads the tile's
-// drifted displacements (in cells) and their mean; the window is the tile's
-// cell block shifted by the rounded mean and padded by TILE_HALO cells.  Pass 2
-// adds each particle's ORDER^3 weights into the window with shared-memory
-// atomics (particles whose taps leave the window add straight to global
-// memory), and the window is flushed with 16-byte vector reductions, skipping
-// all-zero groups.  The x origin is aligned to 4 cells so that every group is
-// 16-byte aligned and never straddles the periodic boundary.
+// A tile is (32/R) x (8/R) x (8/R) lattice sites (R = n_mesh / n_part in {1, 2}),
+// i.e. a 32 x 8 x 8 block of cells before the particles move.  Its window is
+// WX x WY x WZ cells: that block shifted by the tile's rounded mean displacement
+// and padded by DEP_HALO cells (the x origin aligned down to 4 cells, so that
+// every group of 4 cells is 16-byte aligned and never straddles the periodic
+// boundary).  Each particle adds its ORDER^3 weights with shared-memory atomics
+// (particles whose taps leave the window add straight to global memory), and
+// the window is flushed with one 16-byte vector reduction per non-zero group.
 // The window accumulates in unsigned fixed point, weight * 2^20 rounded: integer
 // shared-memory atomics are native (float ones are not), the sums are exact and
 // order-independent, and a cell cannot overflow since at most 2048 particles
 // (one tile) add at most 2^20 each.
-constexpr int TILE_HALO = 4;
+constexpr int DEP_HALO = 3;
 constexpr float DEP_FIX = 1048576.f;            // 2^20
 constexpr float DEP_UNFIX = 1.f / 1048576.f;
 
 template <int ORDER>
 struct DepWindow {
-    static constexpr int LO = ORDER == 3 ? 1 : 0;                           // taps below the base cell
-    static constexpr int WX = (32 + 2 * TILE_HALO + ORDER + 3 + 3) / 4 * 4;   // + alignment slack
-    static constexpr int WY = 8 + 2 * TILE_HALO + ORDER;
-    static constexpr int WZ = WY;
+    static constexpr int LO = ORDER == 3 ? 1 : 0;   // taps below the base cell
+    static constexpr int WX = 44;                   // 32 + 2 halo + ORDER - 1 + alignment slack, rounded to 4
+    static constexpr int WY = 16;                   // 8 + 2 halo + ORDER - 1, rounded up
+    static constexpr int WZ = 16;
+    static constexpr int QX = WX / 4;               // 16-byte groups per window row
     static constexpr int CELLS = WX * WY * WZ;
+    static_assert(QX <= 16 && WY == 16, "flush maps 16 lanes per row, 16 rows per plane");
+    static_assert(32 + 2 * DEP_HALO + ORDER - 1 + 3 <= WX && 8 + 2 * DEP_HALO + ORDER - 1 <= WY, "window");
 };
 
 __device__ __forceinline__ void red_v4(float* p, float4 v) {
@@ -199,143 +209,172 @@ __device__ __forceinline__ void red_v4(float* p, float4 v) {
 }
 
 // Tile geometry of the Lagrangian-tile kernels (R = n_mesh / n_part in {1, 2}).
+// Thread t holds the particles p = 0..PPT-1 at x = ix0 + t % TXP and rows
+// (t / TXP + RSTEP p) of the tile's TYP x TZP lattice rows; RSTEP is a multiple
+// of TYP, so particle p sits p * RSTEP / TYP lattice planes above particle 0.
 template <int R>
 struct TileGeom {
     static constexpr int TXP = 32 / R, TYP = 8 / R, TZP = 8 / R;
     static constexpr int PPT = TXP * TYP * TZP / 256;    // particles per thread
     static constexpr int RSTEP = 256 / TXP;               // rows advanced per particle slot
-    int ix0, iy0, iz0, xp;
-    __device__ TileGeom(int tile, int np) {
-        const int ntx = np / TXP, nty = np / TYP;
-        ix0 = (tile % ntx) * TXP;
-        iy0 = ((tile / ntx) % nty) * TYP;
-        iz0 = (tile / (ntx * nty)) * TZP;
-        xp = threadIdx.x % TXP;
+    static constexpr int DZ = RSTEP / TYP;                // planes advanced per particle slot
+    static_assert(RSTEP % TYP == 0, "tile rows");
+    int ix0, iy0, iz0;   // tile origin (lattice)
+    int ix, iy, iz;      // this thread's particle 0 (lattice)
+    __device__ TileGeom(int tile, int log2np) {
+        constexpr int LX = R == 2 ? 4 : 5, LY = R == 2 ? 2 : 3;   // log2 TXP, log2 TYP (= log2 TZP)
+        const int lnx = log2np - LX, lny = log2np - LY;            // log2 of the tile counts along x, y
+        ix0 = (tile & ((1 << lnx) - 1)) << LX;
+        iy0 = ((tile >> lnx) & ((1 << lny) - 1)) << LY;
+        iz0 = (tile >> (lnx + lny)) << LY;
+        const int r = threadIdx.x / TXP;
+        ix = ix0 + threadIdx.x % TXP;
+        iy = iy0 + r % TYP;
+        iz = iz0 + r / TYP;
     }
-    __device__ int iy(int p) const { return iy0 + (threadIdx.x / TXP + RSTEP * p) % TYP; }
-    __device__ int iz(int p) const { return iz0 + (threadIdx.x / TXP + RSTEP * p) / TYP; }
-    __device__ long long index(int p, int np) const { return ((long long)iz(p) * np + iy(p)) * np + (ix0 + xp); }
 };
 
-// Second half of a tile deposit: the tile mean of the displacements in cells
-// (m0..m2 hold this thread's partial sums), the window placement, the scatter
-// of the thread's PPT particles into the window (or into global memory when
-// their taps leave it), and the flush.  Called by all 256 threads.
+// Persistent tile deposit: CTA b walks tiles b, b + gridDim.x, ...  Per tile the
+// drifted displacements (in cells) are loaded while the next tile's state lines
+// are prefetched into L2, block-reduced to their mean (which places the window),
+// scattered into the window, and the window is flushed.  The flush clears every
+// group it adds to the mesh, so the window is all-zero again for the next tile
+// with no separate clearing pass; the barrier after the first reduction of the
+// next tile orders that clearing before the next atomics.
 template <int ORDER, int R>
-__device__ __forceinline__ void tile_window_deposit(const PmGeom& g, const TileGeom<R>& T, const float* sx,
-                                                    const float* sy, const float* sz, float m0, float m1, float m2,
-                                                    unsigned* win, float (*red)[8], float* __restrict__ m) {
+__global__ void __launch_bounds__(256, 4) k_deposit_tiled(PmGeom g, const float* __restrict__ disp,
+                                                          const float* __restrict__ vel,
+                                                          const SlotCoef* __restrict__ coef, int cstride,
+                                                          float shift, float* __restrict__ rho, int ntiles) {
     using Win = DepWindow<ORDER>;
-    constexpr int PPT = TileGeom<R>::PPT;
+    using TG = TileGeom<R>;
+    constexpr int PPT = TG::PPT;
+    constexpr int DS = R == 2 ? 1 : 0;                    // log2 R
+    extern __shared__ uint4 win4[];
+    unsigned* win = reinterpret_cast<unsigned*>(win4);
+    __shared__ __align__(16) float red[3][8];
+    const int slot = blockIdx.y;
+    const SlotCoef cf = coef[slot * cstride];
+    if (!cf.active) return;
     const int t = threadIdx.x;
+    const int np = 1 << g.log2np;
+    const long long N = 1ll << (3 * g.log2np);
+    const float* dx = disp + slot * g.slot_part;
+    const float* dy = dx + N;
+    const float* dz = dy + N;
+    const float* vx = vel ? vel + slot * g.slot_part : nullptr;
+    float* m = rho + slot * g.slot_mesh;
+    const int log2ng = g.log2ng, ng = 1 << log2ng, msk = ng - 1;
+    const int plane = np * np;                            // lattice sites per plane (< 2^31)
+    for (int i = t; i < Win::CELLS / 4; i += 256) win4[i] = make_uint4(0u, 0u, 0u, 0u);
+    // flush geometry of this thread: group q of row y in every plane
+    const int fq = t & 15, fy = t >> 4;
+
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const TG T(tile, g.log2np);
+        if (tile + (int)gridDim.x < ntiles && t < 3 * TG::TYP * TG::TZP) {
+            // L2 prefetch of the next tile's lattice rows (component, row) of disp (and vel)
+            const TG Tn(tile + gridDim.x, g.log2np);
+            const int c = t / (TG::TYP * TG::TZP), row = t % (TG::TYP * TG::TZP);
+            const long long i0 = c * N + ((long long)(Tn.iz0 + row / TG::TYP) * np + Tn.iy0 + row % TG::TYP) * np + Tn.ix0;
+            prefetch_l2(dx + i0);
+            if (vx) prefetch_l2(vx + i0);
+        }
+        const int i0 = (T.iz * np + T.iy) * np + T.ix;    // particle 0 of this thread
+        float sx[PPT], sy[PPT], sz[PPT];
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        m0 += __shfl_xor_sync(0xffffffffu, m0, o);
-        m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-        m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-    }
-    if ((t & 31) == 0) {
-        red[0][t >> 5] = m0;
-        red[1][t >> 5] = m1;
-        red[2][t >> 5] = m2;
-    }
-    for (int i = t; i < Win::CELLS / 4; i += 256) reinterpret_cast<uint4*>(win)[i] = make_uint4(0u, 0u, 0u, 0u);
-    __syncthreads();
-    float mean[3];
+        for (int p = 0; p < PPT; ++p) {
+            const int i = i0 + p * TG::DZ * plane;
+            float a = dx[i], b = dy[i], c = dz[i];
+            if (vx) {
+                a += cf.tau1 * vx[i];
+                b += cf.tau1 * vx[N + i];
+                c += cf.tau1 * vx[2 * N + i];
+            }
+            sx[p] = a * g.inv_h + shift;
+            sy[p] = b * g.inv_h + shift;
+            sz[p] = c * g.inv_h + shift;
+            m0 += sx[p];
+            m1 += sy[p];
+            m2 += sz[p];
+        }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float sum = 0.f;
+        for (int o = 16; o > 0; o >>= 1) {
+            m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+            m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+            m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        }
+        if ((t & 31) == 0) {
+            red[0][t >> 5] = m0;
+            red[1][t >> 5] = m1;
+            red[2][t >> 5] = m2;
+        }
+        __syncthreads();
+        float mean[3];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) sum += red[c][w];
-        mean[c] = sum * (1.f / (TileGeom<R>::TXP * TileGeom<R>::TYP * TileGeom<R>::TZP));
-    }
-    const int ox = (T.ix0 * R + __float2int_rn(mean[0]) - TILE_HALO - Win::LO) & ~3;
-    const int oy = T.iy0 * R + __float2int_rn(mean[1]) - TILE_HALO - Win::LO;
-    const int oz = T.iz0 * R + __float2int_rn(mean[2]) - TILE_HALO - Win::LO;
-    const int ng = 1 << g.log2ng, msk = ng - 1;
-    const int ds = g.log2ng - g.log2np;
+        for (int c = 0; c < 3; ++c) {
+            const float4 u = reinterpret_cast<const float4*>(red[c])[0];
+            const float4 w = reinterpret_cast<const float4*>(red[c])[1];
+            mean[c] = ((u.x + u.y) + (u.z + u.w) + ((w.x + w.y) + (w.z + w.w))) *
+                      (1.f / (TG::TXP * TG::TYP * TG::TZP));
+        }
+        const int ox = (T.ix0 * R + __float2int_rn(mean[0]) - DEP_HALO - Win::LO) & ~3;
+        const int oy = T.iy0 * R + __float2int_rn(mean[1]) - DEP_HALO - Win::LO;
+        const int oz = T.iz0 * R + __float2int_rn(mean[2]) - DEP_HALO - Win::LO;
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-        const AxisTaps ax = axis_taps<ORDER>(T.ix0 + T.xp, ds, sx[p]);
-        const AxisTaps ay = axis_taps<ORDER>(T.iy(p), ds, sy[p]);
-        const AxisTaps az = axis_taps<ORDER>(T.iz(p), ds, sz[p]);
-        const int lx = ax.c - ox, ly = ay.c - oy, lz = az.c - oz;
-        const bool inside = lx >= 0 && lx + ORDER <= Win::WX && ly >= 0 && ly + ORDER <= Win::WY && lz >= 0 &&
-                            lz + ORDER <= Win::WZ;
-        if (inside) {
+        for (int p = 0; p < PPT; ++p) {
+            const AxisTaps ax = axis_taps<ORDER>(T.ix, DS, sx[p]);
+            const AxisTaps ay = axis_taps<ORDER>(T.iy, DS, sy[p]);
+            const AxisTaps az = axis_taps<ORDER>(T.iz + p * TG::DZ, DS, sz[p]);
+            const int lx = ax.c - ox, ly = ay.c - oy, lz = az.c - oz;
+            const bool inside = (unsigned)lx <= (unsigned)(Win::WX - ORDER) &&
+                                (unsigned)ly <= (unsigned)(Win::WY - ORDER) &&
+                                (unsigned)lz <= (unsigned)(Win::WZ - ORDER);
+            if (inside) {
+                unsigned* w0 = win + (lz * Win::WY + ly) * Win::WX + lx;
 #pragma unroll
-            for (int c = 0; c < ORDER; ++c)
+                for (int c = 0; c < ORDER; ++c) {
+                    const float wz = az.w[c] * DEP_FIX;
 #pragma unroll
-                for (int b = 0; b < ORDER; ++b) {
-                    unsigned* wrow = win + ((lz + c) * Win::WY + (ly + b)) * Win::WX + lx;
-                    const float wzy = az.w[c] * ay.w[b] * DEP_FIX;
+                    for (int b = 0; b < ORDER; ++b) {
+                        const float wzy = wz * ay.w[b];
 #pragma unroll
-                    for (int a = 0; a < ORDER; ++a) atomicAdd(wrow + a, __float2uint_rn(wzy * ax.w[a]));
+                        for (int a = 0; a < ORDER; ++a)
+                            atomicAdd(w0 + (c * Win::WY + b) * Win::WX + a, __float2uint_rn(wzy * ax.w[a]));
+                    }
                 }
-        } else {
+            } else {
 #pragma unroll
-            for (int c = 0; c < ORDER; ++c) {
-                const long long zo = (long long)((az.c + c) & msk) * ng;
+                for (int c = 0; c < ORDER; ++c) {
+                    const long long zo = (long long)((az.c + c) & msk) << log2ng;
 #pragma unroll
-                for (int b = 0; b < ORDER; ++b) {
-                    const long long yo = (zo + ((ay.c + b) & msk)) * ng;
-                    const float wzy = az.w[c] * ay.w[b];
+                    for (int b = 0; b < ORDER; ++b) {
+                        const long long yo = (zo + ((ay.c + b) & msk)) << log2ng;
+                        const float wzy = az.w[c] * ay.w[b];
 #pragma unroll
-                    for (int a = 0; a < ORDER; ++a) atomicAdd(&m[yo + ((ax.c + a) & msk)], wzy * ax.w[a]);
+                        for (int a = 0; a < ORDER; ++a) atomicAdd(&m[yo + ((ax.c + a) & msk)], wzy * ax.w[a]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // flush: this thread's group fq of row fy in each of the WZ planes; clear what it adds
+        if (fq < Win::QX) {
+            const int row = (((oy + fy) & msk) << log2ng) + ((ox + 4 * fq) & msk);
+            uint4* src = win4 + fy * Win::QX + fq;
+#pragma unroll 4
+            for (int z = 0; z < Win::WZ; ++z) {
+                const uint4 u = src[z * Win::WY * Win::QX];
+                if ((u.x | u.y | u.z | u.w) != 0u) {
+                    src[z * Win::WY * Win::QX] = make_uint4(0u, 0u, 0u, 0u);
+                    const float4 val =
+                        make_float4(u.x * DEP_UNFIX, u.y * DEP_UNFIX, u.z * DEP_UNFIX, u.w * DEP_UNFIX);
+                    red_v4(m + ((long long)((oz + z) & msk) << (2 * log2ng)) + row, val);
                 }
             }
         }
     }
-    __syncthreads();
-    // flush: one 16-byte vector reduction per non-zero group of 4 cells
-    constexpr int QX = Win::WX / 4;
-    for (int i = t; i < Win::CELLS / 4; i += 256) {
-        const uint4 u = reinterpret_cast<const uint4*>(win)[i];
-        if ((u.x | u.y | u.z | u.w) == 0u) continue;
-        const float4 val = make_float4(u.x * DEP_UNFIX, u.y * DEP_UNFIX, u.z * DEP_UNFIX, u.w * DEP_UNFIX);
-        const int q = i % QX, yz = i / QX;
-        const int y = yz % Win::WY, z = yz / Win::WY;
-        const long long gi = ((long long)((oz + z) & msk) * ng + ((oy + y) & msk)) * ng + ((ox + 4 * q) & msk);
-        red_v4(m + gi, val);
-    }
-}
-
-template <int ORDER, int R>
-__global__ void __launch_bounds__(256) k_deposit_tiled(PmGeom g, const float* __restrict__ disp,
-                                                       const float* __restrict__ vel,
-                                                       const SlotCoef* __restrict__ coef, int cstride, float shift,
-                                                       float* __restrict__ rho) {
-    constexpr int PPT = TileGeom<R>::PPT;
-    extern __shared__ unsigned win[];
-    __shared__ float red[3][8];
-    const int slot = blockIdx.y;
-    const SlotCoef cf = coef[slot * cstride];
-    if (!cf.active) return;
-    const int np = 1 << g.log2np;
-    const TileGeom<R> T(blockIdx.x, np);
-    const long long N = 1ll << (3 * g.log2np);
-    const float* d = disp + slot * g.slot_part;
-    const float* v = vel ? vel + slot * g.slot_part : nullptr;
-    // pass 1: drifted displacements in cells and their sums
-    float sx[PPT], sy[PPT], sz[PPT];
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-#pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-        const long long i = T.index(p, np);
-        float a = d[i], b = d[N + i], c = d[2 * N + i];
-        if (v) {
-            a += cf.tau1 * v[i];
-            b += cf.tau1 * v[N + i];
-            c += cf.tau1 * v[2 * N + i];
-        }
-        sx[p] = a * g.inv_h + shift;
-        sy[p] = b * g.inv_h + shift;
-        sz[p] = c * g.inv_h + shift;
-        m0 += sx[p];
-        m1 += sy[p];
-        m2 += sz[p];
-    }
-    tile_window_deposit<ORDER, R>(g, T, sx, sy, sz, m0, m1, m2, win, red, rho + slot * g.slot_mesh);
 }
 
 // interpolation + kick + drift_2 from interleaved float4 force meshes [slot][grid][M].
@@ -358,55 +397,63 @@ __global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict
     if (!cf.active) return;
     const float tin = predrift_in ? 0.f : cf.tau1;
     const float tout = cf.tau2 + (coef_next ? coef_next[slot * cstride].tau1 : 0.f);
-    const long long N = 1ll << (3 * g.log2np);
-    const long long i0 = (long long)blockIdx.x * (256 * IK_PPT) + threadIdx.x;
-    float* d = disp + slot * g.slot_part;
-    float* v = vel + slot * g.slot_part;
-    const int ds = g.log2ng - g.log2np;
-    const long long M = 1ll << (3 * g.log2ng);
+    const int N = 1 << (3 * g.log2np);                  // at most 2^30 particles per slot
+    const int i0 = blockIdx.x * (256 * IK_PPT) + threadIdx.x;
+    float* dx = disp + slot * g.slot_part;
+    float* dy = dx + N;
+    float* dz = dy + N;
+    float* vx = vel + slot * g.slot_part;
+    float* vy = vx + N;
+    float* vz = vy + N;
+    const int ds = g.log2ng - g.log2np, l2p = g.log2np, mp = (1 << l2p) - 1;
     const float4* f = force4 + slot * g.slot_mesh;
+    const long long M = 1ll << (3 * g.log2ng);
     float p[IK_PPT][3], u[IK_PPT][3], acc[IK_PPT][3];
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
         for (int k = 0; k < IK_PPT; ++k) {
-            const long long ip = i0 + 256 * k + STATE_PREFETCH;
+            const long long ip = (long long)i0 + 256 * k + STATE_PREFETCH;
             if (ip < N) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    prefetch_l2(&d[c * N + ip]);
-                    prefetch_l2(&v[c * N + ip]);
-                }
+                prefetch_l2(dx + ip);
+                prefetch_l2(dy + ip);
+                prefetch_l2(dz + ip);
+                prefetch_l2(vx + ip);
+                prefetch_l2(vy + ip);
+                prefetch_l2(vz + ip);
             }
         }
     }
 #pragma unroll
     for (int k = 0; k < IK_PPT; ++k) {
-        const long long i = i0 + 256 * k;
+        const int i = i0 + 256 * k;
+        const bool ok = i < N;
+        // the state is touched once per step: stream it past the caches the gathers use
+        u[k][0] = ok ? __ldcs(vx + i) : 0.f;
+        u[k][1] = ok ? __ldcs(vy + i) : 0.f;
+        u[k][2] = ok ? __ldcs(vz + i) : 0.f;
+        p[k][0] = (ok ? __ldcs(dx + i) : 0.f) + tin * u[k][0];      // drift_1: X_half
+        p[k][1] = (ok ? __ldcs(dy + i) : 0.f) + tin * u[k][1];
+        p[k][2] = (ok ? __ldcs(dz + i) : 0.f) + tin * u[k][2];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            // the state is touched once per step: stream it past the caches the gathers use
-            u[k][c] = i < N ? __ldcs(&v[c * N + i]) : 0.f;
-            p[k][c] = (i < N ? __ldcs(&d[c * N + i]) : 0.f) + tin * u[k][c];   // drift_1: X_half
-            acc[k][c] = 0.f;
-        }
+        for (int c = 0; c < 3; ++c) acc[k][c] = 0.f;
     }
 #pragma unroll
     for (int k = 0; k < IK_PPT; ++k) {
-        const long long i = i0 + 256 * k;
+        const int i = i0 + 256 * k;
         if (i >= N) continue;
-        const Lattice L = lattice_index(i, g.log2np);
+        const int ix = i & mp, iy = (i >> l2p) & mp, iz = i >> (2 * l2p);
         {
-            const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[k][0] * g.inv_h);
-            const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[k][1] * g.inv_h);
-            const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[k][2] * g.inv_h);
+            const AxisTaps ax = axis_taps<ORDER>(ix, ds, p[k][0] * g.inv_h);
+            const AxisTaps ay = axis_taps<ORDER>(iy, ds, p[k][1] * g.inv_h);
+            const AxisTaps az = axis_taps<ORDER>(iz, ds, p[k][2] * g.inv_h);
             gather3v<ORDER>(f, g.log2ng, ax, ay, az, acc[k]);
         }
         if (IL) {
             // second grid shifted by half a cell; average the two interpolants
             float acc1[3] = {0.f, 0.f, 0.f};
-            const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[k][0] * g.inv_h + 0.5f);
-            const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[k][1] * g.inv_h + 0.5f);
-            const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[k][2] * g.inv_h + 0.5f);
+            const AxisTaps ax = axis_taps<ORDER>(ix, ds, p[k][0] * g.inv_h + 0.5f);
+            const AxisTaps ay = axis_taps<ORDER>(iy, ds, p[k][1] * g.inv_h + 0.5f);
+            const AxisTaps az = axis_taps<ORDER>(iz, ds, p[k][2] * g.inv_h + 0.5f);
             gather3v<ORDER>(f + M, g.log2ng, ax, ay, az, acc1);
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[k][c] = 0.5f * (acc[k][c] + acc1[c]);
@@ -414,14 +461,17 @@ __global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict
     }
 #pragma unroll
     for (int k = 0; k < IK_PPT; ++k) {
-        const long long i = i0 + 256 * k;
+        const int i = i0 + 256 * k;
         if (i >= N) continue;
+        float vn[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float vn = cf.alpha * u[k][c] + cf.kick * acc[k][c];   // kick
-            __stcs(&v[c * N + i], vn);
-            __stcs(&d[c * N + i], p[k][c] + tout * vn);                   // drift_2 (+ next drift_1)
-        }
+        for (int c = 0; c < 3; ++c) vn[c] = cf.alpha * u[k][c] + cf.kick * acc[k][c];   // kick
+        __stcs(vx + i, vn[0]);
+        __stcs(vy + i, vn[1]);
+        __stcs(vz + i, vn[2]);
+        __stcs(dx + i, p[k][0] + tout * vn[0]);                                        // drift_2 (+ next drift_1)
+        __stcs(dy + i, p[k][1] + tout * vn[1]);
+        __stcs(dz + i, p[k][2] + tout * vn[2]);
     }
 }
 
@@ -758,12 +808,23 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
     if (tiled && (order == 2 || order == 3)) {
         const int np = 1 << g.log2np;
         const unsigned ntiles = (unsigned)((long long)(np / (32 / R)) * (np / (8 / R)) * (np / (8 / R)));
-        dim3 grid(ntiles, nslots);
-#define PM_DT(O, RR)                                                                                      \
-    {                                                                                                     \
-        const int smem = DepWindow<O>::CELLS * (int)sizeof(unsigned);                                        \
-        cudaFuncSetAttribute(k_deposit_tiled<O, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);  \
-        k_deposit_tiled<O, RR><<<grid, 256, smem, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho); \
+#define PM_DT(O, RR)                                                                                        \
+    {                                                                                                       \
+        const int smem = DepWindow<O>::CELLS * (int)sizeof(unsigned);                                          \
+        static int resident[64];                                                                            \
+        int dev = 0;                                                                                        \
+        cudaGetDevice(&dev);                                                                                \
+        if (dev < 0 || dev >= 64) dev = 0;                                                                  \
+        if (!resident[dev]) {                                                                               \
+            cudaFuncSetAttribute(k_deposit_tiled<O, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+            int per_sm = 0, sms = 0;                                                                        \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit_tiled<O, RR>, 256, smem);      \
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);                              \
+            resident[dev] = per_sm * sms > 0 ? per_sm * sms : 1;                                            \
+        }                                                                                                   \
+        dim3 grid(ntiles < (unsigned)resident[dev] ? ntiles : (unsigned)resident[dev], nslots);             \
+        k_deposit_tiled<O, RR><<<grid, 256, smem, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho,  \
+                                                        (int)ntiles);                                            \
     }
         if (order == 2 && R == 1) PM_DT(2, 1)
         else if (order == 2) PM_DT(2, 2)
