@@ -475,6 +475,148 @@ __global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict
     }
 }
 
+// Interpolation + kick + drift_2 along Lagrangian columns (CIC, mesh = lattice,
+// no interlacing).  A CTA takes a 32 x 8 x 8 tile of lattice sites; thread t walks
+// the column of 8 sites at (x, y) = (ix0 + t % 32, iy0 + t / 32) upwards in z.
+// The ORDER planes of force taps (ORDER x ORDER float4 each) of the previous
+// particle stay in registers: when the next particle lies in the same (x, y)
+// cell column, z-shifted by 0..ORDER-1 cells, the planes it shares are reused and
+// only the new ones are gathered (a lattice column that has not crossed cells
+// gathers one plane per particle instead of ORDER).  The next particle's state
+// is loaded while the current one gathers.
+template <int ORDER>
+__global__ void __launch_bounds__(256, 3) k_interp_col(PmGeom g, float* __restrict__ disp, float* __restrict__ vel,
+                                                    const SlotCoef* __restrict__ coef, int cstride,
+                                                    const float4* __restrict__ force4, int predrift_in,
+                                                    const SlotCoef* __restrict__ coef_next) {
+    using TG = TileGeom<1>;
+    constexpr int PPT = TG::PPT;
+    static_assert(TG::DZ == 1, "column walk needs consecutive planes");
+    const int slot = blockIdx.y;
+    const SlotCoef cf = coef[slot * cstride];
+    if (!cf.active) return;
+    const float tin = predrift_in ? 0.f : cf.tau1;
+    const float tout = cf.tau2 + (coef_next ? coef_next[slot * cstride].tau1 : 0.f);
+    const int l2 = g.log2np, msk = (1 << l2) - 1;
+    const int N = 1 << (3 * l2), plane = 1 << (2 * l2);
+    float* dx = disp + slot * g.slot_part;
+    float* dy = dx + N;
+    float* dz = dy + N;
+    float* vx = vel + slot * g.slot_part;
+    float* vy = vx + N;
+    float* vz = vy + N;
+    const float4* f = force4 + slot * g.slot_mesh;
+    const TG T(blockIdx.x, l2);
+    const int i0 = (T.iz * (1 << l2) + T.iy) * (1 << l2) + T.ix;
+    // L2 prefetch of the state of the tile STATE_TILES ahead (one line per lattice row and array)
+    constexpr int STATE_TILES = 32;
+    if (blockIdx.x + STATE_TILES < gridDim.x && threadIdx.x < 64) {
+        const TG Tn(blockIdx.x + STATE_TILES, l2);
+        const int r = threadIdx.x;
+        const int ip = ((Tn.iz0 + r / 8) * (1 << l2) + Tn.iy0 + r % 8) * (1 << l2) + Tn.ix0;
+        prefetch_l2(dx + ip);
+        prefetch_l2(dy + ip);
+        prefetch_l2(dz + ip);
+        prefetch_l2(vx + ip);
+        prefetch_l2(vy + ip);
+        prefetch_l2(vz + ip);
+    }
+    float4 P[ORDER][ORDER][ORDER];   // [z plane][y][x] taps of the previous particle
+#pragma unroll
+    for (int k = 0; k < ORDER; ++k)
+#pragma unroll
+        for (int b = 0; b < ORDER; ++b)
+#pragma unroll
+            for (int a = 0; a < ORDER; ++a) P[k][b][a] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int pcx = -(1 << 30), pcy = 0, pcz = 0;
+    float nd[3], nv[3];
+    nd[0] = __ldcs(dx + i0);
+    nd[1] = __ldcs(dy + i0);
+    nd[2] = __ldcs(dz + i0);
+    nv[0] = __ldcs(vx + i0);
+    nv[1] = __ldcs(vy + i0);
+    nv[2] = __ldcs(vz + i0);
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int i = i0 + p * plane;
+        float u[3], x[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            u[c] = nv[c];
+            x[c] = nd[c] + tin * u[c];             // drift_1: X_half
+        }
+        if (p + 1 < PPT) {
+            const int j = i + plane;
+            nd[0] = __ldcs(dx + j);
+            nd[1] = __ldcs(dy + j);
+            nd[2] = __ldcs(dz + j);
+            nv[0] = __ldcs(vx + j);
+            nv[1] = __ldcs(vy + j);
+            nv[2] = __ldcs(vz + j);
+        }
+        const AxisTaps ax = axis_taps<ORDER>(T.ix, 0, x[0] * g.inv_h);
+        const AxisTaps ay = axis_taps<ORDER>(T.iy, 0, x[1] * g.inv_h);
+        const AxisTaps az = axis_taps<ORDER>(T.iz + p, 0, x[2] * g.inv_h);
+        // planes shared with the previous particle: shift = az.c - pcz in [0, ORDER)
+        const int shift = (ax.c == pcx && ay.c == pcy) ? az.c - pcz : ORDER;
+        const bool keep = shift >= 0 && shift < ORDER;
+#pragma unroll
+        for (int k = 0; k + 1 < ORDER; ++k) {
+#pragma unroll
+            for (int b = 0; b < ORDER; ++b)
+#pragma unroll
+                for (int a = 0; a < ORDER; ++a) {
+                    float4 v = P[k][b][a];
+                    if (shift == 1) v = P[k + 1][b][a];
+                    if (ORDER == 3 && k == 0 && shift == 2) v = P[ORDER - 1][b][a];
+                    P[k][b][a] = v;
+                }
+        }
+        int xo[ORDER], yo[ORDER];
+#pragma unroll
+        for (int a = 0; a < ORDER; ++a) {
+            xo[a] = (ax.c + a) & msk;
+            yo[a] = ((ay.c + a) & msk) << l2;
+        }
+#pragma unroll
+        for (int k = 0; k < ORDER; ++k) {
+            if (!keep || k + shift >= ORDER) {
+                const int zo = ((az.c + k) & msk) << (2 * l2);
+#pragma unroll
+                for (int b = 0; b < ORDER; ++b)
+#pragma unroll
+                    for (int a = 0; a < ORDER; ++a) P[k][b][a] = __ldg(f + (zo + yo[b] + xo[a]));
+            }
+        }
+        pcx = ax.c;
+        pcy = ay.c;
+        pcz = az.c;
+        float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < ORDER; ++k)
+#pragma unroll
+            for (int b = 0; b < ORDER; ++b) {
+                const float wzy = az.w[k] * ay.w[b];
+#pragma unroll
+                for (int a = 0; a < ORDER; ++a) {
+                    const float w = wzy * ax.w[a];
+                    acc[0] += w * P[k][b][a].x;
+                    acc[1] += w * P[k][b][a].y;
+                    acc[2] += w * P[k][b][a].z;
+                }
+            }
+        float vn[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vn[c] = cf.alpha * u[c] + cf.kick * acc[c];   // kick
+        __stcs(vx + i, vn[0]);
+        __stcs(vy + i, vn[1]);
+        __stcs(vz + i, vn[2]);
+        __stcs(dx + i, x[0] + tout * vn[0]);                                        // drift_2 (+ next drift_1)
+        __stcs(dy + i, x[1] + tout * vn[1]);
+        __stcs(dz + i, x[2] + tout * vn[2]);
+    }
+}
+
 template <int ORDER, int IL, int KICK>
 __global__ void __launch_bounds__(256) k_interp(PmGeom g, float* __restrict__ disp, float* __restrict__ vel,
                                                 const SlotCoef* __restrict__ coef, int cstride,
@@ -847,6 +989,11 @@ int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float
                    int coef_stride, const float4* force4, int nslots, cudaStream_t st, int predrift_in,
                    const SlotCoef* coef_next) {
     const long long N = 1ll << (3 * g.log2np);
+    if (order == 2 && !interlace && g.log2ng == g.log2np && g.log2np >= 5) {
+        dim3 gt((unsigned)(N / 2048), nslots);
+        k_interp_col<2><<<gt, 256, 0, st>>>(g, disp, vel, coef, coef_stride, force4, predrift_in, coef_next);
+        return 0;
+    }
     dim3 grid((unsigned)((N + 256 * IK_PPT - 1) / (256 * IK_PPT)), nslots);
 #define PM_IK(O, I) k_interp_kick<O, I><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, force4, predrift_in, coef_next)
     if (order == 2 && !interlace) PM_IK(2, 0);
