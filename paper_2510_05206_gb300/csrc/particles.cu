@@ -711,6 +711,115 @@ __global__ void __launch_bounds__(256) k_grad_stencil(int log2n, float inv_h, co
     out[blockIdx.y * f_stride + j] = make_float4(g[0], g[1], g[2], 0.f);
 }
 
+// Same gradient through shared-memory planes: a CTA owns a 32 x 16 column of
+// cells over GS_ZC consecutive planes.  It marches up in z: the potential of its
+// own cells at z - R .. z + R sits in a register queue (the z derivative), plane
+// z with an R-cell x/y halo sits in shared memory (the x and y derivatives), and
+// the next plane's values are loaded while the current one is differentiated.
+// Every potential value is read from global memory about once per CTA (plus the
+// halo and the 2R planes before the column), instead of 3 * GO times.
+constexpr int GS_TX = 32, GS_TY = 16, GS_ZC = 32;
+template <int GO>
+__global__ void __launch_bounds__(256) k_grad_stencil_t(int log2n, float inv_h, const float* __restrict__ phi,
+                                                        long long phi_stride, float4* __restrict__ out,
+                                                        long long f_stride) {
+    constexpr int R = GO / 2, SX = GS_TX + 2 * R, SY = GS_TY + 2 * R;
+    constexpr int NH = 2 * R * (GS_TX + GS_TY), HPT = (NH + 255) / 256;   // halo cells per plane, per thread
+    const float c1 = (GO == 2 ? 0.5f : (GO == 4 ? 8.f / 12.f : 45.f / 60.f)) * inv_h;
+    const float c2 = (GO == 4 ? -1.f / 12.f : -9.f / 60.f) * inv_h;
+    const float c3 = (1.f / 60.f) * inv_h;
+    __shared__ float s[2][SY][SX];
+    const int n = 1 << log2n, msk = n - 1, l2n = 2 * log2n;
+    const int nzc = n / GS_ZC;
+    const int slot = blockIdx.z / nzc, z0 = (blockIdx.z % nzc) * GS_ZC;
+    const int x0 = blockIdx.x * GS_TX, y0 = blockIdx.y * GS_TY;
+    const float* f = phi + slot * phi_stride;
+    float4* o = out + slot * f_stride;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;          // cells (tx, ty) and (tx, ty + 8)
+    const int row0 = (((y0 + ty) & msk) << log2n) + ((x0 + tx) & msk);
+    const int row1 = (((y0 + ty + 8) & msk) << log2n) + ((x0 + tx) & msk);
+    // halo cells of this thread: shared-memory slot and in-plane offset
+    int hs[HPT], hg[HPT];
+#pragma unroll
+    for (int k = 0; k < HPT; ++k) {
+        const int h = threadIdx.x + 256 * k;
+        int sr = 0, sc = 0, gx = 0, gy = 0;
+        if (h < 2 * R * GS_TY) {
+            const int side = h / (R * GS_TY), rem = h % (R * GS_TY), r = rem / R, c = rem % R;
+            sr = r + R;
+            sc = side ? GS_TX + R + c : c;
+            gx = x0 + (side ? GS_TX + c : c - R);
+            gy = y0 + r;
+        } else if (h < NH) {
+            const int h2 = h - 2 * R * GS_TY;
+            const int side = h2 / (R * GS_TX), rem = h2 % (R * GS_TX), r = rem / GS_TX, c = rem % GS_TX;
+            sr = side ? GS_TY + R + r : r;
+            sc = c + R;
+            gx = x0 + c;
+            gy = y0 + (side ? GS_TY + r : r - R);
+        }
+        hs[k] = h < NH ? sr * SX + sc : -1;
+        hg[k] = ((gy & msk) << log2n) + (gx & msk);
+    }
+    auto plane = [&](int z) { return (long long)(z & msk) << l2n; };
+    // register queues of the column values at z - R .. z + R, and the halo of plane z
+    float q0[2 * R + 1], q1[2 * R + 1], hv[HPT];
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) {
+        const long long p = plane(z0 - R + k);
+        q0[k] = __ldg(f + p + row0);
+        q1[k] = __ldg(f + p + row1);
+    }
+#pragma unroll
+    for (int k = 0; k < HPT; ++k) hv[k] = hs[k] >= 0 ? __ldg(f + plane(z0) + hg[k]) : 0.f;
+    for (int zi = 0; zi < GS_ZC; ++zi) {
+        const int z = z0 + zi, b = zi & 1;
+        float* sb = &s[b][0][0];
+        sb[(ty + R) * SX + tx + R] = q0[R];
+        sb[(ty + 8 + R) * SX + tx + R] = q1[R];
+#pragma unroll
+        for (int k = 0; k < HPT; ++k)
+            if (hs[k] >= 0) sb[hs[k]] = hv[k];
+        // next plane's loads in flight during this plane's differences
+        float n0 = 0.f, n1 = 0.f;
+        if (zi + 1 < GS_ZC) {
+            const long long pn = plane(z + R + 1);
+            n0 = __ldg(f + pn + row0);
+            n1 = __ldg(f + pn + row1);
+#pragma unroll
+            for (int k = 0; k < HPT; ++k) hv[k] = hs[k] >= 0 ? __ldg(f + plane(z + 1) + hg[k]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const float* q = half ? q1 : q0;
+            const int sy = ty + 8 * half + R, sx = tx + R;
+            const float* srow = sb + sy * SX + sx;
+            float gx = c1 * (srow[1] - srow[-1]);
+            float gy = c1 * (srow[SX] - srow[-SX]);
+            float gz = c1 * (q[R + 1] - q[R - 1]);
+            if (R >= 2) {
+                gx += c2 * (srow[2] - srow[-2]);
+                gy += c2 * (srow[2 * SX] - srow[-2 * SX]);
+                gz += c2 * (q[R + 2] - q[R - 2]);
+            }
+            if (R >= 3) {
+                gx += c3 * (srow[3] - srow[-3]);
+                gy += c3 * (srow[3 * SX] - srow[-3 * SX]);
+                gz += c3 * (q[R + 3] - q[R - 3]);
+            }
+            o[plane(z) + (half ? row1 : row0)] = make_float4(-gx, -gy, -gz, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) {
+            q0[k] = q0[k + 1];
+            q1[k] = q1[k + 1];
+        }
+        q0[2 * R] = n0;
+        q1[2 * R] = n1;
+    }
+}
+
 // div[q][j] = sum_c D1_c s_c at every cell for three planar meshes s_c (q < nmesh,
 // s slot stride s_stride floats, c-th mesh at c * M; div slot stride d_stride).
 // Its transpose pairs with k_grad_stencil: D1 is antisymmetric, so the adjoint
@@ -1069,6 +1178,15 @@ int pm_axpby(float* out, const float* x, const float* y, float a, float b, long 
 int pm_grad_stencil(int grad_order, int log2n, float inv_h, const float* phi, long long phi_stride, float4* force4,
                     long long f_stride, int nmesh, cudaStream_t st) {
     const long long M = 1ll << (3 * log2n);
+    if (log2n >= 5) {
+        const int n = 1 << log2n;
+        dim3 gt(n / GS_TX, n / GS_TY, (n / GS_ZC) * nmesh);
+        if (grad_order == 2) k_grad_stencil_t<2><<<gt, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
+        else if (grad_order == 4) k_grad_stencil_t<4><<<gt, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
+        else if (grad_order == 6) k_grad_stencil_t<6><<<gt, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
+        else return -1;
+        return 0;
+    }
     dim3 grid((unsigned)((M + 255) / 256), nmesh);
     if (grad_order == 2) k_grad_stencil<2><<<grid, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
     else if (grad_order == 4) k_grad_stencil<4><<<grid, 256, 0, st>>>(log2n, inv_h, phi, phi_stride, force4, f_stride);
