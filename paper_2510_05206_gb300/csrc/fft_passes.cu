@@ -259,50 +259,43 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
 
     if (MODE == Z_PK) {
         // sum over the modes of each bin of w |delta^|^2 (w = 2 for 0 < kx < n/2, the
-        // half spectrum standing for +-kx), FP64: lanes of a warp that share a bin are
-        // reduced with shuffles, then one shared-memory atomic per bin and warp, then
-        // one global atomic per bin and CTA.  Mode counts and mean |k| per bin depend
-        // on the mesh only and are tabulated exactly on the host.
+        // half spectrum standing for +-kx), FP64 per bin: runs of equal bin along kz
+        // are summed per thread, then added to a per-warp (or shared) FP64 accumulator
+        // in shared memory, then one global atomic per bin and CTA.  Mode counts and
+        // mean |k| per bin depend on the mesh only and are tabulated exactly on the host.
         // per-warp private FP64 accumulators when they fit (no contention between
         // warps), else one shared set updated atomically
         double* acc = reinterpret_cast<double*>(B.s);
         constexpr int NW = (1 << LOG2N) >= 32 ? (1 << LOG2N) / 32 : 1;
-        // blocks of n < 32 threads are a partial warp: synchronise only its lanes
-        constexpr unsigned FULL = (1 << LOG2N) >= 32 ? 0xffffffffu : ((1u << (1 << LOG2N)) - 1u);
         const bool priv = NW * a.nbins <= TE;
         const int nacc = priv ? NW * a.nbins : a.nbins;
         for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0.0;
         __syncthreads();
-        const int lane = threadIdx.x & 31;
         double* wacc = priv ? acc + (threadIdx.x >> 5) * a.nbins : acc;
-        constexpr int T = n * COL_TILE;
-        for (int i = threadIdx.x; i < T; i += blockDim.x) {   // T is a multiple of blockDim: no divergence
-            const int e = i / COL_TILE, l = i % COL_TILE;
-            const int kx = kx0 + l;
-            int b = -1;
-            float v = 0.f;
-            if (kx <= n / 2) {
-                const int mz = freq_index(e, n);
-                b = __ldg(&a.bintab[kx * kx + my * my + mz * mz]);
-                const float2 d = A(l, e);
-                v = ((kx == 0 || kx == n / 2) ? 1.f : 2.f) * (d.x * d.x + d.y * d.y);
-            }
-            // the float sum of at most 32 lanes feeds an FP64 per-bin accumulator
-            unsigned todo = __ballot_sync(FULL, b >= 0);
-            while (todo) {
-                const int leader = __ffs(todo) - 1;
-                const int bl = __shfl_sync(FULL, b, leader);
-                const bool mine = (b == bl);
-                float sv = mine ? v : 0.f;
+        // thread: column l, COL_TILE consecutive kz planes.  Along a column |k| is monotone
+        // on each side of kz = n/2, so the bin changes rarely: sum in FP32 while it stays,
+        // and add each finished run to the FP64 bin accumulator.
+        constexpr int CH = COL_TILE;                       // n * COL_TILE elements / n threads
+        const int l = threadIdx.x % COL_TILE, e0 = (threadIdx.x / COL_TILE) * CH;
+        const int kx = kx0 + l;
+        if (kx <= n / 2) {
+            const float wx = (kx == 0 || kx == n / 2) ? 1.f : 2.f;
+            const int kxy = kx * kx + my * my;
+            int cur = -1;
+            float run = 0.f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    if (o < (1 << LOG2N)) sv += __shfl_xor_sync(FULL, sv, o);
-                if (lane == leader) {
-                    if (priv) wacc[bl] += (double)sv;
-                    else atomicAdd(&wacc[bl], (double)sv);
+            for (int k = 0; k < CH; ++k) {
+                const int e = e0 + k, mz = freq_index(e, n);
+                const int bk = __ldg(&a.bintab[kxy + mz * mz]);
+                const float2 d = A(l, e);
+                if (bk != cur) {
+                    if (cur >= 0) atomicAdd(&wacc[cur], (double)run);
+                    cur = bk;
+                    run = 0.f;
                 }
-                todo &= ~__ballot_sync(FULL, mine);
+                run += wx * (d.x * d.x + d.y * d.y);
             }
+            if (cur >= 0) atomicAdd(&wacc[cur], (double)run);
         }
         __syncthreads();
         if (priv)
