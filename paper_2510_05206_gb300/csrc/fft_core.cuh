@@ -136,12 +136,12 @@ __device__ __forceinline__ void fft_lines(float2* s, const float2* tw, int twstr
 // fly) and end in global memory without an extra shared-memory round trip.
 // Middle stages work in place on the shared-memory tile `sm`.
 
-template <int N, int R, int NS, int NL, int DIR, bool MIDSYNC, class Ld, class St>
-__device__ __forceinline__ void stage_io(const Ld& ld, const St& st, const float2* tw, int twstride, bool active) {
+// The loads of one stage: thread (line, j) takes v[b R + r] = element j + b N/8 + r N/R.
+template <int N, int R, int NL, class Ld>
+__device__ __forceinline__ void stage_load(const Ld& ld, float2 v[8], bool active) {
     constexpr int NB = 8 / R;
     const int line = threadIdx.x % NL;
     const int j = threadIdx.x / NL;
-    float2 v[8];
     if (active) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -150,7 +150,14 @@ __device__ __forceinline__ void stage_io(const Ld& ld, const St& st, const float
             for (int r = 0; r < R; ++r) v[b * R + r] = ld(line, jj + r * (N / R));
         }
     }
-    if (MIDSYNC) __syncthreads();
+}
+
+// The twiddles, butterflies and stores of one stage on loaded values v.
+template <int N, int R, int NS, int NL, int DIR, class St>
+__device__ __forceinline__ void stage_cs(float2 v[8], const St& st, const float2* tw, int twstride, bool active) {
+    constexpr int NB = 8 / R;
+    const int line = threadIdx.x % NL;
+    const int j = threadIdx.x / NL;
     if (active) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -169,6 +176,14 @@ __device__ __forceinline__ void stage_io(const Ld& ld, const St& st, const float
             for (int r = 0; r < R; ++r) st(line, o + r * NS, vb[r]);
         }
     }
+}
+
+template <int N, int R, int NS, int NL, int DIR, bool MIDSYNC, class Ld, class St>
+__device__ __forceinline__ void stage_io(const Ld& ld, const St& st, const float2* tw, int twstride, bool active) {
+    float2 v[8];
+    stage_load<N, R, NL>(ld, v, active);
+    if (MIDSYNC) __syncthreads();
+    stage_cs<N, R, NS, NL, DIR>(v, st, tw, twstride, active);
 }
 
 // radix of stage i (0-based) and Ns before it for an N-point transform
@@ -203,6 +218,33 @@ __device__ __forceinline__ void fft_io(const Ld& ld, const St& st, const Sm& sm,
         __syncthreads();
     }
     static_assert(Pl::S <= 4, "at most 4 stages (N <= 4096)");
+    stage_io<N, Pl::radix(Pl::S - 1), Pl::ns(Pl::S - 1), NL, DIR, LAST_SMEM>(sm, st, tw, twstride, active);
+}
+
+// First-stage inputs of fft_pre (the loads fft_io's first stage makes), so that a
+// caller can have the next transform's loads in flight during the current one.
+template <int N, int NL, class Ld>
+__device__ __forceinline__ void fft_first_load(const Ld& ld, float2 v[8]) {
+    stage_load<N, Plan<N>::radix(0), NL>(ld, v, threadIdx.x < NL * N / 8);
+}
+
+// fft_io from first-stage inputs already in registers.  The first stage writes
+// `sm`, so the caller puts a barrier between any earlier reader of `sm` and this.
+template <int N, int NL, int DIR, bool LAST_SMEM, class St, class Sm>
+__device__ __forceinline__ void fft_pre(float2 v[8], const St& st, const Sm& sm, const float2* tw, int twstride) {
+    using Pl = Plan<N>;
+    static_assert(Pl::S >= 2, "N must have at least two stages");
+    const bool active = threadIdx.x < NL * N / 8;
+    stage_cs<N, Pl::radix(0), 1, NL, DIR>(v, sm, tw, twstride, active);
+    __syncthreads();
+    if constexpr (Pl::S > 2) {
+        stage_io<N, Pl::radix(1), Pl::ns(1), NL, DIR, true>(sm, sm, tw, twstride, active);
+        __syncthreads();
+    }
+    if constexpr (Pl::S > 3) {
+        stage_io<N, Pl::radix(2), Pl::ns(2), NL, DIR, true>(sm, sm, tw, twstride, active);
+        __syncthreads();
+    }
     stage_io<N, Pl::radix(Pl::S - 1), Pl::ns(Pl::S - 1), NL, DIR, LAST_SMEM>(sm, st, tw, twstride, active);
 }
 

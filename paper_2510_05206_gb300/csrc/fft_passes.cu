@@ -163,18 +163,32 @@ __global__ void __launch_bounds__(768) k_fft_x_c2r3(const float2* __restrict__ i
 // n = 512 instead of four.
 __host__ __device__ constexpr int col_min_blocks(int log2n) { return (1024 >> log2n) > 32 ? 32 : ((1024 >> log2n) < 1 ? 1 : (1024 >> log2n)); }
 
-// y pass: grid (tiles, n planes, meshes)
+// y pass: grid (tile groups, n planes, meshes).  A CTA transforms Y_TPC column
+// tiles of one plane in turn, with the next tile's first-stage loads in flight
+// during the current tile's transform.
+constexpr int Y_TPC = 3;
 template <int LOG2N, int DIR>
 __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_y(float2* __restrict__ data, long long stride,
                                                                             const float2* __restrict__ twg) {
-    constexpr int n = 1 << LOG2N, P = n / 2 + SPEC_PAD;
+    constexpr int n = 1 << LOG2N, P = n / 2 + SPEC_PAD, NT = P / COL_TILE;
     extern __shared__ float2 sm[];
     float2* tw = sm;
     const ColTile tile{sm + n};
     for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
-    const GCols g{data + blockIdx.z * stride + (long long)blockIdx.y * n * P + blockIdx.x * COL_TILE, P};
-    // the first stage needs no twiddles; the barrier after it publishes them
-    fft_io<n, COL_TILE, DIR, false, false>(g, g, tile, tw, 1);
+    float2* base = data + blockIdx.z * stride + (long long)blockIdx.y * n * P;
+    const int t0 = blockIdx.x * Y_TPC, t1 = t0 + Y_TPC < NT ? t0 + Y_TPC : NT;
+    float2 nxt[8];
+    fft_first_load<n, COL_TILE>(GCols{base + t0 * COL_TILE, P}, nxt);
+    for (int t = t0; t < t1; ++t) {
+        float2 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = nxt[k];
+        if (t + 1 < t1) fft_first_load<n, COL_TILE>(GCols{base + (t + 1) * COL_TILE, P}, nxt);
+        // the first stage needs no twiddles; the barrier after it publishes them
+        const GCols g{base + t * COL_TILE, P};
+        fft_pre<n, COL_TILE, DIR, false>(v, g, tile, tw, 1);
+        __syncthreads();   // the next tile's first stage overwrites what the last stage read
+    }
 }
 
 // ---------------------------------------------------------------- z pass
@@ -432,7 +446,8 @@ template <int LOG2N>
 void launch_y(float2* data, long long stride, int nmesh, int dir, const float2* tw, cudaStream_t st) {
     constexpr int n = 1 << LOG2N;
     const size_t smem = (size_t)(col_tile_elems(n) + n) * sizeof(float2);
-    dim3 grid(n / 2 / COL_TILE + 1, n, nmesh);
+    constexpr int NT = (n / 2 + SPEC_PAD) / COL_TILE;
+    dim3 grid((NT + Y_TPC - 1) / Y_TPC, n, nmesh);
     if (dir < 0) {
         set_smem(k_fft_y<LOG2N, -1>, smem);
         k_fft_y<LOG2N, -1><<<grid, n, smem, st>>>(data, stride, tw);
