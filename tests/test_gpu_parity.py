@@ -48,6 +48,43 @@ def test_density_deposit(n_part, n_mesh, order):
     assert abs(delta.sum()) < 1e-4 * n_mesh ** 3 ** 0.5 + 1e-3
 
 
+@pytest.mark.parametrize("n_part,n_mesh,order", [(32, 32, 2), (64, 64, 2), (32, 32, 3), (32, 64, 2), (32, 64, 3)])
+def test_density_deposit_structured(n_part, n_mesh, order):
+    # tile-window paths of the deposit: jittered columns, collapsed columns (many
+    # particles per cell) and particles far outside their tile's window
+    L = 100.0
+    pm = PM(Config(n_part=n_part, n_mesh=n_mesh, box=L, order=order), device=DEV)
+    Psi = inputs.structured_displacements(n_part, L / n_mesh, seed=11)
+    delta = _np(pm.density(_t(Psi[None]), n_mesh, order))[0]
+    X = np.mod(nbody.lattice(n_part, L) + Psi, L)
+    ref = mesh.density_contrast(X, n_mesh, L, order)
+    assert _rel_max(delta, ref) < 2e-5
+    assert abs(delta.sum()) < 1e-4 * n_mesh ** 3 ** 0.5 + 1e-3
+
+
+@pytest.mark.parametrize("n,order,pre", [(32, 2, 0), (64, 2, 0), (32, 2, 1), (32, 3, 0)])
+def test_kick_drift_structured(n, order, pre):
+    # one DKD step from structured positions through the column-walk interpolation
+    # (CIC, mesh = lattice: tap planes reused for columns in the same or next cell)
+    # against the oracle step; pre = 1 carries pre-drifted positions (a 2-step run)
+    L = 64.0
+    kw = dict(n_part=n, n_mesh=n, box=L, order=order, n_steps=2)
+    pm = PM(Config(**kw), device=DEV)
+    Psi = inputs.structured_displacements(n, L / n, seed=12)
+    V = inputs.random_displacements(n, scale=0.3, seed=13)
+    d, v = _t(Psi[None]), _t(V[None])
+    ocfg = nbody.Config(**kw)
+    tab = cosmology.step_table(ocfg.get_growth(), ocfg.a_ini, ocfg.a_end, 2)
+    P1, V1 = nbody.step(ocfg, Psi, V, tab[0], nbody.lattice(n, L))
+    if pre:
+        pm.run(d, v, 0, 2)
+        P1, V1 = nbody.step(ocfg, P1, V1, tab[1], nbody.lattice(n, L))
+    else:
+        pm.step(d, v, 0)
+    assert _disp_err(_np(d)[0], P1) < 1e-4
+    assert _disp_err(_np(v)[0], V1) < 1e-4
+
+
 @pytest.mark.parametrize("n,grad,lap", [(32, 4, 0), (64, 4, 0), (32, 0, 0), (32, 2, 2), (16, 6, 4), (128, 4, 0)])
 def test_force_mesh(n, grad, lap):
     L = 300.0
