@@ -21,7 +21,7 @@ using namespace pmfft;
 template <int LOG2N>
 __global__ void __launch_bounds__(256) k_fft_x_r2c(const float* __restrict__ in, long long in_stride,
                                                    float2* __restrict__ out, long long out_stride,
-                                                   const float2* __restrict__ twg) {
+                                                   const float2* __restrict__ twg, int clear_in) {
     constexpr int n = 1 << LOG2N, N = n / 2, P = N + SPEC_PAD;
     constexpr int ROWS = (2048 / N) < n * n ? (2048 / N) : n * n;
     constexpr int LS = N + 1;
@@ -37,6 +37,13 @@ __global__ void __launch_bounds__(256) k_fft_x_r2c(const float* __restrict__ in,
         const float4 v = src[i];
         tile[r * LS + 2 * c] = make_float2(v.x, v.y);
         tile[r * LS + 2 * c + 1] = make_float2(v.z, v.w);
+    }
+    if (clear_in) {
+        // a consumed density mesh is left zeroed for the next deposit (after all the
+        // loads above are issued: stores in the load loop would serialise them)
+        __syncthreads();
+        float4* dstz = reinterpret_cast<float4*>(const_cast<float*>(in) + q * in_stride + row0 * n);
+        for (int i = threadIdx.x; i < ROWS * N / 2; i += blockDim.x) dstz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     fft_lines<N, ROWS, LS, 1, -1>(tile, tw, 2);
@@ -406,13 +413,13 @@ int rows_per_cta() {
 
 template <int LOG2N>
 void launch_x_r2c(const float* in, long long in_stride, float2* out, long long out_stride, int nmesh,
-                  const float2* tw, cudaStream_t st) {
+                  const float2* tw, int clear_in, cudaStream_t st) {
     constexpr int n = 1 << LOG2N, N = n / 2;
     const int rows = rows_per_cta<LOG2N>();
     const size_t smem = (size_t)(rows * (N + 1) + n) * sizeof(float2);
     set_smem(k_fft_x_r2c<LOG2N>, smem);
     dim3 grid(n * n / rows, nmesh);
-    k_fft_x_r2c<LOG2N><<<grid, 256, smem, st>>>(in, in_stride, out, out_stride, tw);
+    k_fft_x_r2c<LOG2N><<<grid, 256, smem, st>>>(in, in_stride, out, out_stride, tw, clear_in);
 }
 
 template <int LOG2N>
@@ -497,8 +504,8 @@ void launch_z(int mode, const ZArgs& a, int nslots, cudaStream_t st) {
     }
 
 int pm_fft_r2c_x(int log2n, const float* in, long long in_stride, float2* out, long long out_stride, int nmesh,
-                 const float2* tw, cudaStream_t st) {
-    PM_DISPATCH_LOG2N(log2n, (launch_x_r2c<LG>(in, in_stride, out, out_stride, nmesh, tw, st)));
+                 const float2* tw, cudaStream_t st, int clear_in) {
+    PM_DISPATCH_LOG2N(log2n, (launch_x_r2c<LG>(in, in_stride, out, out_stride, nmesh, tw, clear_in, st)));
     return 0;
 }
 

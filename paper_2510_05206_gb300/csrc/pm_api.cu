@@ -237,13 +237,13 @@ PmGeom geom(const pm_handle* h, int nmesh, long long slot_mesh) {
 // Forward real FFT of ngrids density meshes per slot (rho, slot stride rho_slot)
 // into spectra comp 0..ngrids-1; then the fused z pass producing ncomp spectra.
 int spectral_force(pm_handle* h, const float* src, long long src_slot, long long src_grid, float scale,
-                   float* force_out, float4* force4, int nslots) {
+                   float* force_out, float4* force4, int nslots, int clear_src = 0) {
     const int n = h->ng, l2 = ilog2i(n);
     const long long S = spec_elems(n), SS = (long long)h->ncomp * S;
     cudaStream_t st = h->stream;
     h->phase(1, h->ngrids);
     for (int g = 0; g < h->ngrids; ++g)
-        if (pm_fft_r2c_x(l2, src + g * src_grid, src_slot, h->spec + g * S, SS, nslots, h->d_tw[l2], st))
+        if (pm_fft_r2c_x(l2, src + g * src_grid, src_slot, h->spec + g * S, SS, nslots, h->d_tw[l2], st, clear_src))
             return h->fail(PM_ERR_ARG, "unsupported mesh size %d", n);
     h->phase_end();
     h->phase(2, h->ngrids);
@@ -269,15 +269,17 @@ int spectral_force(pm_handle* h, const float* src, long long src_slot, long long
         h->phase(4, h->ngrids);
         for (int g = 0; g < h->ngrids; ++g) pm_fft_y(l2, h->spec + g * S, SS, nslots, 1, h->d_tw[l2], st);
         h->phase_end();
-        // the potential overwrites the density (already transformed)
+        // the real potential of grid g goes to the unused spectrum slot ngrids + g (a
+        // spectrum slot holds more than n^3 floats), so the density mesh stays as the
+        // forward x pass left it
+        auto phi = [&](int g) { return reinterpret_cast<float*>(h->spec + (h->ngrids + g) * S); };
         h->phase(5, h->ngrids);
         for (int g = 0; g < h->ngrids; ++g)
-            pm_fft_c2r_x(l2, h->spec + g * S, SS, h->rho + g * h->Mg(), h->rho_slot(), nullptr, 0, 0.f, nslots,
-                         h->d_tw[l2], st);
+            pm_fft_c2r_x(l2, h->spec + g * S, SS, phi(g), 2 * SS, nullptr, 0, 0.f, nslots, h->d_tw[l2], st);
         h->phase_end();
         h->phase(11, h->ngrids);
         for (int g = 0; g < h->ngrids; ++g)
-            pm_grad_stencil(go, l2, (float)(n / h->cfg.box), h->rho + g * h->Mg(), h->rho_slot(), force4 + g * h->Mg(),
+            pm_grad_stencil(go, l2, (float)(n / h->cfg.box), phi(g), 2 * SS, force4 + g * h->Mg(),
                             (long long)h->ngrids * h->Mg(), nslots, st);
         h->phase_end();
         return h->check_launch("force spectral passes");
@@ -635,7 +637,8 @@ int pm_run(pm_handle* h, float* disp, float* vel, int32_t b, int32_t e) {
     const PmGeom gd = geom(h, h->ng, h->rho_slot());
     const PmGeom gf = geom(h, h->ng, Mg);
     for (int s = b; s < e; ++s) {
-        if (cudaMemsetAsync(h->rho, 0, sizeof(float) * h->rho_slot() * h->B, st) != cudaSuccess)
+        // later steps find the density zeroed by the previous step's forward x pass
+        if (s == b && cudaMemsetAsync(h->rho, 0, sizeof(float) * h->rho_slot() * h->B, st) != cudaSuccess)
             return h->fail(PM_ERR_CUDA, "memset density");
         h->phase(0, 1);
         if (s == b)
@@ -643,7 +646,8 @@ int pm_run(pm_handle* h, float* disp, float* vel, int32_t b, int32_t e) {
         else
             pm_deposit(h->cfg.order, gd, disp, nullptr, h->d_unit, 0, 0.f, h->rho, h->B, st);
         h->phase_end();
-        int rc = spectral_force(h, h->rho, h->rho_slot(), Mg, (float)(1.0 / (double)h->Np()), nullptr, h->force, h->B);
+        int rc = spectral_force(h, h->rho, h->rho_slot(), Mg, (float)(1.0 / (double)h->Np()), nullptr, h->force, h->B,
+                                s + 1 < e);
         if (rc) return rc;
         h->phase(6, 1);
         pm_interp_kick(h->cfg.order, 0, gf, disp, vel, h->d_table + s, 0, h->force, h->B, st, s > b,

@@ -23,8 +23,10 @@ struct PmZPass {
 enum { PM_Z_FORCE = 0, PM_Z_FORCE_IL = 1, PM_Z_IC = 2, PM_Z_PK = 3, PM_Z_ADJ = 4, PM_Z_IC_ADJ = 5, PM_Z_POT = 6,
        PM_Z_POT_IL = 7 };
 
+// clear_in != 0: the input rows are zeroed after they are read (a density mesh
+// consumed here is then ready for the next deposit without a separate memset)
 int pm_fft_r2c_x(int log2n, const float* in, long long in_stride, float2* out, long long out_stride, int nmesh,
-                 const float2* tw, cudaStream_t st);
+                 const float2* tw, cudaStream_t st, int clear_in = 0);
 int pm_fft_c2r_x(int log2n, const float2* in, long long in_stride, float* out, long long out_stride, float* out2,
                  long long out2_stride, float scale2, int nmesh, const float2* tw, cudaStream_t st);
 // inverse x pass of three spectra (comp_stride apart; slot q at q * slot_stride) into one
