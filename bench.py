@@ -121,16 +121,19 @@ def measured_traffic(kernel):
     return None
 
 
-def algorithmic_bytes(n_part, n_mesh):
+def algorithmic_bytes(n_part, n_mesh, n_steps=6):
     """Compulsory HBM bytes per launch of each phase (float32; M = mesh cells,
-    N = particles; complex half spectra count as M/2 complex = 4M bytes)."""
+    N = particles; complex half spectra count as M/2 complex = 4M bytes),
+    averaged over the launches of one run of n_steps steps."""
     N, M = n_part ** 3, n_mesh ** 3
+    later = (n_steps - 1) / n_steps          # share of the steps after the first
     return {
         # deposit: the first step of a run reads disp and vel (24 N), the later ones
-        # the carried pre-drifted positions only (12 N): 14 N per launch on average over
-        # 6 steps; the density is written once (4 M)
-        "deposit": 14 * N + 4 * M,
-        "fft_x_fwd": 4 * M + 4 * M,              # read real mesh, write half spectrum
+        # the carried pre-drifted positions only (12 N); the density is written once (4 M)
+        "deposit": (24 - 12 * later) * N + 4 * M,
+        # read the real mesh, write the half spectrum; inside a run (all but the last
+        # step) the consumed density is also cleared for the next deposit (4 M)
+        "fft_x_fwd": 4 * M + 4 * M + 4 * M * later,
         "fft_y_fwd": 8 * M,                      # read + write half spectrum
         # finite-difference gradient (grad_order 2/4/6): the z pass maps the density
         # spectrum to the potential's, one inverse transform, then the stencil
@@ -401,7 +404,7 @@ def main():
                "ms_per_step": e2e_s * 1e3 / args.e2e_steps}
 
     # roofline of the dominant kernel (largest share of the timed region)
-    alg = algorithmic_bytes(n, cfg.n_mesh)
+    alg = algorithmic_bytes(n, cfg.n_mesh, cfg.n_steps)
     peak, peak_kind = measured_peaks()
     kernels = {}
     for name, p in prof.items():
