@@ -302,6 +302,36 @@ def scaleup_benchmark(dev, reps=3):
             "ms_per_pm_step": ms / 10, "particle_steps_per_s": n ** 3 * 10 / (ms / 1e3)}
 
 
+def deconvolve_benchmark(dev, reps=3):
+    """The 512^3 workload with the force density deconvolved by the squared CIC
+    kernel (N_g = N with deconvolution): ICs + 6 BullFrog steps."""
+    import numpy as np
+    import torch
+    from paper_2510_05206_gb300 import PM, Config
+    n = WORKLOAD["n_part"]
+    pm = PM(Config(n_part=n, n_mesh=WORKLOAD["n_mesh"], box=WORKLOAD["box_mpc_h"], n_steps=6, deconvolve=1),
+            device=dev)
+    rng = np.random.default_rng(NOISE_SEED)
+    noise = torch.from_numpy(rng.standard_normal((1, n ** 3), dtype=np.float32)).to(dev)
+    disp, vel = pm.new_state()
+    for _ in range(3):
+        pm.ic_zeldovich(noise, disp, vel)
+        pm.run(disp, vel)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        pm.ic_zeldovich(noise, disp, vel)
+        pm.run(disp, vel)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    pm.close()
+    return {"workload": f"pm_{n}cubed_6step_cic_deconvolved", "ms_per_run": ms, "ms_per_pm_step": ms / 6,
+            "particle_steps_per_s": n ** 3 * 6 / (ms / 1e3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,6 +463,7 @@ def main():
     if not args.no_extra:
         line["adjoint"] = adjoint_benchmark(dev)
         line["scaleup"] = scaleup_benchmark(dev)
+        line["deconvolve"] = deconvolve_benchmark(dev)
     if not args.no_serving:
         line["serving"] = serving_benchmark(args.serve_requests, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -64,11 +64,16 @@ typedef struct pm_config {
     int32_t zero_corner; /* 1 = zero initial modes with |k| > k_Nyquist (App. A.3; default 1) */
     int32_t batch;       /* number of simulation slots served by the handle (>= 1) */
     int32_t pk_mesh_max; /* largest mesh pm_power_spectrum may use (0 = n_mesh) */
+    int32_t deconvolve;  /* 1 = divide the force's density spectrum by the squared mass
+                            assignment kernel, prod_c W^(k_c)^2 with W^ = sinc^p(k/2) of
+                            Table 1 (Sec. 2.5, deconvolution of the interpolation kernel;
+                            Table 4 `deconvolve`, default 0) */
 } pm_config;
 
 /* Fills *cfg with the defaults: CIC, no interlacing, 4th-order gradient, exact
  * Laplacian, Omega_m 0.3, h 0.7, n_s 0.96, sigma8 0.8, a 0.02 -> 1, 6 BullFrog
- * steps uniform in D, corner modes zeroed, batch 1; n_part = n_mesh = 64, L = 256. */
+ * steps uniform in D, corner modes zeroed, no deconvolution, batch 1; n_part = n_mesh = 64,
+ * L = 256. */
 void pm_config_default(pm_config* cfg);
 
 /* Device bytes pm_init will allocate for cfg (for admission control). */

@@ -203,7 +203,23 @@ def laplace_kernel_1d(k, H, order):
     raise ValueError(order)
 
 
-def force_multipliers(n, L, grad_order, lap_order, zero_all_nyquist=False):
+def kernel_fourier_1d(k, H, order):
+    """Fourier transform of the 1D mass assignment kernel of order p (Table 1):
+    W^(k) = sinc^p(kt / 2) with sinc(x) = sin(pi x)/(pi x) and kt = k / k_Ny,
+    k_Ny = pi / H (the table's units), i.e. [sin(k H/2) / (k H/2)]^p."""
+    kt = k / (math.pi / H)
+    return np.sinc(0.5 * kt) ** order
+
+
+def deconvolution_1d(k, H, order):
+    """1 / W^(k)^2 per axis: dividing the density by the squared kernel undoes the
+    smoothing of the deposit and of the interpolation back to the particles
+    (Sec. 2.5, deconvolution of the interpolation kernel).  Finite up to the
+    Nyquist mode, where W^ = (2/pi)^p."""
+    return 1.0 / kernel_fourier_1d(k, H, order) ** 2
+
+
+def force_multipliers(n, L, grad_order, lap_order, zero_all_nyquist=False, deconvolve_order=0):
     """m_c(k) with g_c^ = m_c delta^, i.e. g = -grad Lap^-1 delta (Sec. 2.5, Computing the forces).
 
     phi^ = delta^ / K_lap(k),  g_c^ = -D1(k_c) phi^.
@@ -213,6 +229,8 @@ def force_multipliers(n, L, grad_order, lap_order, zero_all_nyquist=False):
     on its Nyquist plane (k_c = n/2), where an odd kernel cannot give a real
     field.  With ``zero_all_nyquist`` every mode on any Nyquist plane is zeroed
     (used with interlacing, whose half-cell phase is not Hermitian there).
+    ``deconvolve_order`` p > 0 also divides by the squared 3D kernel, the product
+    over the axes of W^(k_c)^2 for the order-p kernel.
     Returns a list of 3 complex arrays of shape (n, n, n) [z, y, x].
     """
     H = L / n
@@ -223,6 +241,8 @@ def force_multipliers(n, L, grad_order, lap_order, zero_all_nyquist=False):
     with np.errstate(divide="ignore", invalid="ignore"):
         inv_lap = np.where(lap != 0.0, 1.0 / lap, 0.0)
     inv_lap[0, 0, 0] = 0.0
+    if deconvolve_order:
+        inv_lap = inv_lap * np.prod([deconvolution_1d(kc, H, deconvolve_order) for kc in kk], axis=0)
     idx = np.arange(n)
     nyq = (idx == n // 2)
     nz, ny, nx = np.meshgrid(nyq, nyq, nyq, indexing="ij")
@@ -246,10 +266,12 @@ def apply_multiplier(field, m):
     return out.real
 
 
-def force_field(delta, L, grad_order, lap_order):
-    """g_c = -d_c Lap^-1 delta on the mesh (units of length), c = x, y, z."""
+def force_field(delta, L, grad_order, lap_order, deconvolve_order=0):
+    """g_c = -d_c Lap^-1 delta on the mesh (units of length), c = x, y, z;
+    deconvolve_order p > 0 first divides delta^ by the squared order-p kernel."""
     n = delta.shape[0]
-    return [apply_multiplier(delta, m) for m in force_multipliers(n, L, grad_order, lap_order)]
+    return [apply_multiplier(delta, m)
+            for m in force_multipliers(n, L, grad_order, lap_order, deconvolve_order=deconvolve_order)]
 
 
 def interlace_phase(n, L, sign):

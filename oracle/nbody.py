@@ -34,7 +34,12 @@ class Config:
     stepper: str = "bullfrog"
     time_var: str = "D"
     zero_corner: bool = True
+    deconvolve: bool = False    # divide the force's density by the squared kernel (Table 4 `deconvolve`)
     growth: object = field(default=None, repr=False)
+
+    @property
+    def deconv_order(self):
+        return self.order if self.deconvolve else 0
 
     def get_growth(self):
         if self.growth is None:
@@ -110,7 +115,7 @@ def accel(cfg, Psi, q, Dh):
     X = np.mod(q + Psi, L)
     if not cfg.interlace:
         delta = mesh.density_contrast(X, n, L, cfg.order)
-        g = mesh.force_field(delta, L, cfg.grad_order, cfg.lap_order)
+        g = mesh.force_field(delta, L, cfg.grad_order, cfg.lap_order, cfg.deconv_order)
         A = np.stack([mesh.gather(gc, X, L, cfg.order) for gc in g])
     else:
         H = L / n
@@ -118,7 +123,8 @@ def accel(cfg, Psi, q, Dh):
         d0 = np.fft.fftn(mesh.density_contrast(X, n, L, cfg.order))
         d1 = np.fft.fftn(mesh.density_contrast(X, n, L, cfg.order, shift=s))
         dk = 0.5 * (d0 + mesh.interlace_phase(n, L, +1) * d1)
-        ms = mesh.force_multipliers(n, L, cfg.grad_order, cfg.lap_order, zero_all_nyquist=True)
+        ms = mesh.force_multipliers(n, L, cfg.grad_order, cfg.lap_order, zero_all_nyquist=True,
+                                    deconvolve_order=cfg.deconv_order)
         back = mesh.interlace_phase(n, L, -1)
         A = []
         for m in ms:
@@ -174,7 +180,7 @@ def accel_vjp(cfg, Psi_h, q, Dh, u):
     N = Psi_h.shape[1]
     X = np.mod(q + Psi_h, L)
     delta = mesh.density_contrast(X, n, L, cfg.order)
-    ms = mesh.force_multipliers(n, L, cfg.grad_order, cfg.lap_order)
+    ms = mesh.force_multipliers(n, L, cfg.grad_order, cfg.lap_order, deconvolve_order=cfg.deconv_order)
     g = [mesh.apply_multiplier(delta, m) for m in ms]
     out = np.zeros((3, N))
     for c in range(3):

@@ -206,6 +206,7 @@ struct ZArgs {
     const float2* tw;         // exp(-2 pi i m / n), m < n
     const float* lap1;        // 1D Laplacian kernel per bin (Table 2)
     const float* grad1;       // Im of the 1D gradient kernel per bin, 0 on the Nyquist bin
+    const float* dec1;        // deconvolution 1 / W^(k)^2 per bin of one axis, or NULL
     const float* ictab;       // IC: sqrt(P(k) M / L^3) / (D(1) k^2) / M per integer k^2 index (0 if masked)
     const int* bintab;        // P(k): bin of each integer k^2 index (-1 = none)
     double* pk_out;           // P(k): [slot][3][nbins] (sum w|d|^2, sum w|k|, sum w)
@@ -214,10 +215,14 @@ struct ZArgs {
     float kf;                 // 2 pi / L
 };
 
-enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5, Z_POT = 6, Z_POT_IL = 7 };
+enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5, Z_POT = 6, Z_POT_IL = 7, Z_DEC = 8 };
 
-template <int LOG2N, int MODE>
+// MODE_DEC = mode | Z_DEC: the mode's multiplier also divides by the squared mass
+// assignment kernel (deconvolution tables in a.dec1), compiled only where used.
+template <int LOG2N, int MODE_DEC>
 __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZArgs a) {
+    constexpr int MODE = MODE_DEC & (Z_DEC - 1);
+    constexpr bool deconv = (MODE_DEC & Z_DEC) != 0;
     constexpr int n = 1 << LOG2N, P = n / 2 + SPEC_PAD;
     constexpr int TE = col_tile_elems(n);
     constexpr long long ES = (long long)n * P;      // z stride (complex)
@@ -225,14 +230,17 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
     float2* tw = sm;
     float* lap = reinterpret_cast<float*>(sm + n);
     float* grad = lap + n;
-    const ColTile A{sm + 2 * n};
-    const ColTile B{sm + 2 * n + TE};
-    const ColTile A2{sm + 2 * n + 2 * TE};
+    float* dec = grad + n;                          // deconvolution: n floats = n/2 float2
+    constexpr int T0 = 2 * n + (deconv ? n / 2 : 0);   // tiles after the tables
+    const ColTile A{sm + T0};
+    const ColTile B{sm + T0 + TE};
+    const ColTile A2{sm + T0 + 2 * TE};
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         tw[i] = a.tw[i];
         if (MODE == Z_FORCE || MODE == Z_FORCE_IL || MODE == Z_ADJ || MODE == Z_POT || MODE == Z_POT_IL) {
             lap[i] = a.lap1[i];
             grad[i] = a.grad1[i];
+            if (deconv) dec[i] = a.dec1[i];
         }
     }
     const int slot = blockIdx.z;
@@ -255,7 +263,8 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
             const int kx = kx0 + l;
             float2 r = make_float2(0.f, 0.f);
             if (MODE == Z_ADJ && kx <= n / 2 && (kx | y | e)) {
-                const float inv = a.scale / (lap[kx] + lap[y] + lap[e]);
+                float inv = a.scale / (lap[kx] + lap[y] + lap[e]);
+                if constexpr (deconv) inv *= dec[kx] * dec[y] * dec[e];
                 const float2 s3 = cadd(cadd(cscale(A(l, e), grad[kx]), cscale(B(l, e), grad[y])), cscale(A2(l, e), grad[e]));
                 r = cmul_i(cscale(s3, inv), 1);
             }
@@ -352,7 +361,9 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
                     d = cscale(cadd(d, cmul(make_float2(cs, sn), A2(l, e))), 0.5f);
                     if (gi == 1) d = cmul(d, make_float2(cs, -sn));
                 }
-                return cscale(d, a.scale / (lap[kx] + lap[y] + lap[e]));
+                float f = a.scale / (lap[kx] + lap[y] + lap[e]);
+                if constexpr (deconv) f *= dec[kx] * dec[y] * dec[e];
+                return cscale(d, f);
             };
             fft_io<n, COL_TILE, 1, false, false>(mult, GCols{a.out[gi] + off, ES}, B, tw, 1);
             __syncthreads();
@@ -390,7 +401,8 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
                 if (c >= 3) d = cmul(d, make_float2(cs, -sn));   // grid 1: g^ exp(-i k.s)
             }
             if (keep) {
-                const float f = -grad[bc] * a.scale / (lap[kx] + lap[y] + lap[e]);
+                float f = -grad[bc] * a.scale / (lap[kx] + lap[y] + lap[e]);
+                if constexpr (deconv) f *= dec[kx] * dec[y] * dec[e];
                 r = cmul_i(cscale(d, f), 1);
             }
             return r;
@@ -467,8 +479,9 @@ void launch_y(float2* data, long long stride, int nmesh, int dir, const float2* 
 template <int LOG2N, int MODE>
 void launch_z_mode(const ZArgs& a, int nslots, cudaStream_t st) {
     constexpr int n = 1 << LOG2N;
-    const int ntile = (MODE == Z_FORCE_IL || MODE == Z_ADJ || MODE == Z_IC_ADJ || MODE == Z_POT_IL) ? 3 : 2;
-    const size_t smem = (size_t)(ntile * col_tile_elems(n) + 2 * n) * sizeof(float2);
+    constexpr int M = MODE & (Z_DEC - 1);
+    const int ntile = (M == Z_FORCE_IL || M == Z_ADJ || M == Z_IC_ADJ || M == Z_POT_IL) ? 3 : 2;
+    const size_t smem = (size_t)(ntile * col_tile_elems(n) + 2 * n + ((MODE & Z_DEC) ? n / 2 : 0)) * sizeof(float2);
     dim3 grid(n / 2 / COL_TILE + 1, n, nslots);
     set_smem(k_fft_z<LOG2N, MODE>, smem);
     k_fft_z<LOG2N, MODE><<<grid, n, smem, st>>>(a);
@@ -476,15 +489,31 @@ void launch_z_mode(const ZArgs& a, int nslots, cudaStream_t st) {
 
 template <int LOG2N>
 void launch_z(int mode, const ZArgs& a, int nslots, cudaStream_t st) {
+    const bool dec = a.dec1 != nullptr;
     switch (mode) {
-        case Z_FORCE: launch_z_mode<LOG2N, Z_FORCE>(a, nslots, st); break;
-        case Z_FORCE_IL: launch_z_mode<LOG2N, Z_FORCE_IL>(a, nslots, st); break;
+        case Z_FORCE:
+            if (dec) launch_z_mode<LOG2N, Z_FORCE | Z_DEC>(a, nslots, st);
+            else launch_z_mode<LOG2N, Z_FORCE>(a, nslots, st);
+            break;
+        case Z_FORCE_IL:
+            if (dec) launch_z_mode<LOG2N, Z_FORCE_IL | Z_DEC>(a, nslots, st);
+            else launch_z_mode<LOG2N, Z_FORCE_IL>(a, nslots, st);
+            break;
         case Z_IC: launch_z_mode<LOG2N, Z_IC>(a, nslots, st); break;
         case Z_PK: launch_z_mode<LOG2N, Z_PK>(a, nslots, st); break;
-        case Z_ADJ: launch_z_mode<LOG2N, Z_ADJ>(a, nslots, st); break;
+        case Z_ADJ:
+            if (dec) launch_z_mode<LOG2N, Z_ADJ | Z_DEC>(a, nslots, st);
+            else launch_z_mode<LOG2N, Z_ADJ>(a, nslots, st);
+            break;
         case Z_IC_ADJ: launch_z_mode<LOG2N, Z_IC_ADJ>(a, nslots, st); break;
-        case Z_POT: launch_z_mode<LOG2N, Z_POT>(a, nslots, st); break;
-        case Z_POT_IL: launch_z_mode<LOG2N, Z_POT_IL>(a, nslots, st); break;
+        case Z_POT:
+            if (dec) launch_z_mode<LOG2N, Z_POT | Z_DEC>(a, nslots, st);
+            else launch_z_mode<LOG2N, Z_POT>(a, nslots, st);
+            break;
+        case Z_POT_IL:
+            if (dec) launch_z_mode<LOG2N, Z_POT_IL | Z_DEC>(a, nslots, st);
+            else launch_z_mode<LOG2N, Z_POT_IL>(a, nslots, st);
+            break;
     }
 }
 
@@ -534,6 +563,7 @@ int pm_fft_z(int log2n, int mode, const PmZPass& p, int nslots, cudaStream_t st)
     a.tw = p.tw;
     a.lap1 = p.lap1;
     a.grad1 = p.grad1;
+    a.dec1 = p.dec1;
     a.ictab = p.ictab;
     a.bintab = p.bintab;
     a.pk_out = p.pk_out;

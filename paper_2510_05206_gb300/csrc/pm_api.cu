@@ -55,6 +55,7 @@ struct pm_handle {
     float2* d_tw[11] = {};       // twiddles exp(-2 pi i m / 2^l)
     float* d_lap = nullptr;      // [ng]
     float* d_grad = nullptr;     // [ng]
+    float* d_dec = nullptr;      // [ng] deconvolution 1 / W^(k)^2 per axis, NULL when off
     float* d_ictab = nullptr;    // [3 (np/2)^2 + 1]
     double* d_pk = nullptr;      // [B][pk_bins_cap]: sum over each bin of w |rho^|^2
     int pk_bins_cap = 0;
@@ -166,6 +167,7 @@ int validate(const pm_config* c, std::string& why) {
     if (!(c->box > 0)) return bad("box must be > 0");
     if (c->order != 2 && c->order != 3) return bad("order must be 2 (CIC) or 3 (TSC)");
     if (c->interlace != 0 && c->interlace != 1) return bad("interlace must be 0 or 1");
+    if (c->deconvolve != 0 && c->deconvolve != 1) return bad("deconvolve must be 0 or 1");
     for (int o : {c->grad_order, c->lap_order})
         if (o != 0 && o != 2 && o != 4 && o != 6) return bad("grad_order / lap_order must be 0, 2, 4 or 6");
     if (!(c->omega_m > 0 && c->omega_m <= 1)) return bad("omega_m must be in (0, 1]");
@@ -256,6 +258,7 @@ int spectral_force(pm_handle* h, const float* src, long long src_slot, long long
     z.tw = h->d_tw[l2];
     z.lap1 = h->d_lap;
     z.grad1 = h->d_grad;
+    z.dec1 = h->d_dec;
     z.scale = scale;
     z.kf = (float)(2.0 * M_PI / h->cfg.box);
     const int go = h->cfg.grad_order;
@@ -414,6 +417,7 @@ void pm_config_default(pm_config* c) {
     c->zero_corner = 1;
     c->batch = 1;
     c->pk_mesh_max = 0;
+    c->deconvolve = 0;
 }
 
 int pm_workspace_bytes(const pm_config* cfg, size_t* bytes) {
@@ -494,6 +498,19 @@ int pm_init(const pm_config* cfg, void* stream, pm_handle** out) {
         if ((rc = dalloc(h.get(), &h->d_grad, n, "gradient kernel"))) return bail(rc);
         cudaMemcpy(h->d_lap, lap.data(), n * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(h->d_grad, grad.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+        if (cfg->deconvolve) {
+            // Table 1: W^ = sinc^p(kt/2), sinc(x) = sin(pi x)/(pi x), kt = k/k_Ny = 2 m / n;
+            // the deposit and the interpolation each apply it once: divide by W^2
+            std::vector<float> dec(n);
+            for (int j = 0; j < n; ++j) {
+                const int m = j < n / 2 ? j : j - n;
+                const double x = M_PI * m / n;                 // pi kt / 2
+                const double s = m == 0 ? 1.0 : std::sin(x) / x;
+                dec[j] = (float)std::pow(s, -2.0 * cfg->order);
+            }
+            if ((rc = dalloc(h.get(), &h->d_dec, n, "deconvolution kernel"))) return bail(rc);
+            cudaMemcpy(h->d_dec, dec.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+        }
     }
     {
         // Zel'dovich multiplier per integer |m|^2 = s (k = 2 pi sqrt(s) / L):
@@ -538,6 +555,7 @@ void pm_destroy(pm_handle* h) {
     for (auto* p : h->d_tw) cudaFree(p);
     cudaFree(h->d_lap);
     cudaFree(h->d_grad);
+    cudaFree(h->d_dec);
     cudaFree(h->d_ictab);
     cudaFree(h->d_pk);
     for (auto& kv : h->bintabs) cudaFree(kv.second.d_tab);
@@ -825,6 +843,7 @@ int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adisp, float* avel,
             z.tw = h->d_tw[l2];
             z.lap1 = h->d_lap;
             z.grad1 = h->d_grad;
+            z.dec1 = h->d_dec;
             z.scale = (float)(1.0 / (double)h->Np());
             pm_fft_z(l2, PM_Z_POT, z, h->B, st);
             pm_fft_y(l2, h->spec, S, h->B, 1, h->d_tw[l2], st);
@@ -839,6 +858,7 @@ int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adisp, float* avel,
             z.tw = h->d_tw[l2];
             z.lap1 = h->d_lap;
             z.grad1 = h->d_grad;
+            z.dec1 = h->d_dec;
             z.scale = (float)(1.0 / (double)h->Np());
             pm_fft_z(l2, PM_Z_ADJ, z, h->B, st);
             pm_fft_y(l2, h->spec, 3 * S, h->B, 1, h->d_tw[l2], st);

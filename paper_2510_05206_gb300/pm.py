@@ -31,6 +31,7 @@ class Config:
     zero_corner: int = 1
     batch: int = 1
     pk_mesh_max: int = 0
+    deconvolve: int = 0         # divide the force density by the squared kernel (Table 1 W^)
 
     def to_c(self):
         c = _lib.PmConfig()

@@ -31,11 +31,12 @@ def test_config_default_matches_table4(lib):
     c = _lib.PmConfig()
     lib.pm_config_default(ctypes.byref(c))
     assert (c.order, c.grad_order, c.lap_order, c.stepper, c.time_var, c.zero_corner) == (2, 4, 0, 0, 0, 1)
-    assert c.batch == 1
+    assert c.batch == 1 and c.deconvolve == 0
 
 
 @pytest.mark.parametrize("field,value", [("n_part", 48), ("n_mesh", 2048), ("order", 5), ("grad_order", 3),
-                                         ("batch", 0), ("a_end", 0.01), ("box", -1.0), ("n_steps", 0)])
+                                         ("batch", 0), ("a_end", 0.01), ("box", -1.0), ("n_steps", 0),
+                                         ("deconvolve", 2)])
 def test_invalid_config_rejected(lib, field, value):
     c = Config(n_part=32, n_mesh=32)
     setattr(c, field, value)

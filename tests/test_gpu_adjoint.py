@@ -68,13 +68,14 @@ def test_adjoint_gradient_matches_oracle(order):
         assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 2e-3
 
 
-@pytest.mark.parametrize("grad,lap", [(0, 0), (2, 2), (6, 4), (4, 0)])
-def test_adjoint_gradient_kernels_match_oracle(grad, lap):
+@pytest.mark.parametrize("grad,lap,dec", [(0, 0, 0), (2, 2, 0), (6, 4, 0), (4, 0, 0), (4, 0, 1), (0, 0, 1)])
+def test_adjoint_gradient_kernels_match_oracle(grad, lap, dec):
     # the transposed force operator for the exact i k gradient (three forward
     # transforms, conj multipliers) and for the Table 2 finite differences
-    # (divergence stencil, one potential solve)
+    # (divergence stencil, one potential solve); dec = 1 adds the deconvolution
+    # (a real, even multiplier: its own transpose)
     n, L, sigma = 32, 200.0, 0.1
-    kw = dict(n_part=n, n_mesh=n, box=L, order=3, n_steps=3, grad_order=grad, lap_order=lap)
+    kw = dict(n_part=n, n_mesh=n, box=L, order=3, n_steps=3, grad_order=grad, lap_order=lap, deconvolve=dec)
     pm = PM(Config(**kw), device=DEV)
     ocfg = nbody.Config(**kw)
     w = inputs.white_noise(n, seed=36)

@@ -85,13 +85,17 @@ def test_kick_drift_structured(n, order, pre):
     assert _disp_err(_np(v)[0], V1) < 1e-4
 
 
-@pytest.mark.parametrize("n,grad,lap", [(32, 4, 0), (64, 4, 0), (32, 0, 0), (32, 2, 2), (16, 6, 4), (128, 4, 0)])
-def test_force_mesh(n, grad, lap):
+@pytest.mark.parametrize("n,grad,lap,order,dec", [(32, 4, 0, 2, 0), (64, 4, 0, 2, 0), (32, 0, 0, 2, 0),
+                                                   (32, 2, 2, 2, 0), (16, 6, 4, 2, 0), (128, 4, 0, 2, 0),
+                                                   (32, 4, 0, 2, 1), (32, 0, 0, 3, 1), (64, 6, 2, 3, 1)])
+def test_force_mesh(n, grad, lap, order, dec):
+    # dec = 1: the density spectrum is divided by the squared order-p kernel (Table 1)
     L = 300.0
-    pm = PM(Config(n_part=n, n_mesh=n, box=L, grad_order=grad, lap_order=lap), device=DEV)
+    pm = PM(Config(n_part=n, n_mesh=n, box=L, grad_order=grad, lap_order=lap, order=order, deconvolve=dec),
+            device=DEV)
     d = inputs.random_field(n, seed=2)
     g = _np(pm.force_mesh(_t(d[None])))[0]
-    ref = mesh.force_field(d, L, grad, lap)
+    ref = mesh.force_field(d, L, grad, lap, deconvolve_order=order if dec else 0)
     for c in range(3):
         assert _rel_max(g[c], ref[c]) < 2e-5, c
 
@@ -131,7 +135,8 @@ def _run_pair(cfg_kw, seed, n_bins=None):
     okw = dict(n_part=cfg.n_part, n_mesh=cfg.n_mesh, box=cfg.box, order=cfg.order,
                interlace=bool(cfg.interlace), grad_order=cfg.grad_order, lap_order=cfg.lap_order,
                n_steps=cfg.n_steps, a_ini=cfg.a_ini, a_end=cfg.a_end,
-               stepper=["bullfrog", "fastpm"][cfg.stepper], time_var=["D", "a"][cfg.time_var])
+               stepper=["bullfrog", "fastpm"][cfg.stepper], time_var=["D", "a"][cfg.time_var],
+               deconvolve=bool(cfg.deconvolve))
     ocfg = nbody.Config(**okw)
     P0, V0 = nbody.zeldovich_ic(ocfg, w)
     P1, V1 = nbody.run(ocfg, P0, V0)
@@ -165,6 +170,8 @@ def test_full_run_config1_parity():
     dict(n_part=32, n_mesh=32, box=256.0, order=2, n_steps=3, grad_order=0),                # exact i k gradient
     dict(n_part=32, n_mesh=64, box=200.0, order=2, n_steps=3, grad_order=6, lap_order=4),
     dict(n_part=32, n_mesh=32, box=150.0, order=2, interlace=1, n_steps=3, grad_order=0),   # 6 inverse FFTs
+    dict(n_part=32, n_mesh=32, box=256.0, order=2, n_steps=6, deconvolve=1),                 # option (ii): N_g = N + deconv.
+    dict(n_part=32, n_mesh=32, box=200.0, order=3, n_steps=4, deconvolve=1, interlace=1),
 ])
 def test_full_run_variants_parity(kw):
     pm, disp, vel, P1, V1 = _run_pair(kw, seed=2)

@@ -43,6 +43,49 @@ def test_kernel_fourier_transform_table1(order, p):
         assert val == pytest.approx(np.sinc(kt / 2.0) ** p, abs=1e-12)
 
 
+@pytest.mark.parametrize("order", [2, 3])
+def test_kernel_fourier_1d_is_the_aliased_deposit_spectrum(order):
+    # Poisson summation: the DFT of one particle's deposit at sub-cell offset x0 is
+    # sum_m W^(k + 2 pi m / H) exp(-i (k + 2 pi m / H) x0) (on the ky = kz = 0 line,
+    # i.e. the deposit summed over y and z); averaged over 1024 evenly spaced offsets
+    # the cross terms m != m' vanish unless m - m' is a multiple of 1024, so
+    # E|rho^(k)|^2 = sum_m W^(k_m)^2 to ~1e-7 -- an independent check of Table 1's
+    # W^ = sinc^p(k/2) (units, the pi in sinc, the power p)
+    n, L = 16, 16.0
+    H = L / n
+    offs = (np.arange(1024) + 0.5) / 1024 * H
+    acc = np.zeros(n)
+    for x0 in offs:
+        X = np.array([[3 * H + x0], [0.0], [0.0]])
+        rho = mesh.scatter(X, None, n, L, order).sum(axis=(0, 1))
+        acc += np.abs(np.fft.fft(rho)) ** 2
+    acc /= len(offs)
+    k = mesh.wavenumbers(n, L)
+    ms = np.arange(-400, 401)
+    expected = sum(mesh.kernel_fourier_1d(k + 2 * math.pi * m / H, H, order) ** 2 for m in ms)
+    np.testing.assert_allclose(acc, expected, rtol=2e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_deconvolved_force_multiplier(order):
+    # deconvolution divides by the squared 3D kernel: ratio -> 1 as k -> 0, and on a
+    # Nyquist plane of one axis the factor is (pi/2)^(2p) (Table 1: W^ = (2/pi)^p at kt = 1)
+    n, L = 16, 40.0
+    plain = mesh.force_multipliers(n, L, 4, 0)
+    dec = mesh.force_multipliers(n, L, 4, 0, deconvolve_order=order)
+    h = n // 2
+    # x component at (kx, ky, kz) = (1, 0, 0): ratio 1 / sinc^(2p)(1/16) (close to 1)
+    r1 = dec[0][0, 0, 1] / plain[0][0, 0, 1]
+    assert 1.0 < r1 < 1.05
+    np.testing.assert_allclose(r1, (math.sin(math.pi / 16) / (math.pi / 16)) ** (-2 * order), rtol=1e-12)
+    # y component on the kx = Nyquist plane at ky = 1 (the x-gradient vanishes there)
+    r2 = dec[1][0, 1, h] / plain[1][0, 1, h]
+    np.testing.assert_allclose(r2, (math.pi / 2) ** (2 * order) * (math.sin(math.pi / 16) / (math.pi / 16)) ** (-2 * order),
+                               rtol=1e-12)
+    # k = 0 stays zero
+    assert dec[0][0, 0, 0] == 0 and dec[2][0, 0, 0] == 0
+
+
 @pytest.mark.parametrize("order", [2, 3, 4])
 def test_kernel_derivative_matches_finite_difference(order):
     xs = np.array([-1.7, -1.2, -0.8, -0.3, 0.2, 0.6, 1.1, 1.6])
