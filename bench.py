@@ -13,6 +13,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -177,8 +178,25 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def host_cpu():
+    """CPU model and logical core count of the host the oracle runs on."""
+    model = platform.processor() or platform.machine()
+    try:
+        for ln in open("/proc/cpuinfo"):
+            key = ln.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part", "hardware"):
+                model = ln.split(":", 1)[1].strip()
+                if key == "model name":
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count(), "machine": platform.machine()}
+
+
 def cpu_baseline_sample():
-    """Oracle timing on the host (rank 0, N = 1): ICs + 2 DKD steps at 128^3."""
+    """Oracle timing on the host (rank 0, N = 1): ICs + 2 DKD steps at 128^3,
+    and the 32^3 parity configuration in full."""
+    import numpy as np
     from oracle import cosmology, nbody
     from paper_2510_05206_gb300 import inputs
     n = 128
@@ -191,9 +209,21 @@ def cpu_baseline_sample():
     for i in range(2):
         P, V = nbody.step(cfg, P, V, tab[i], q)
     dt = time.perf_counter() - t0
+    # the 32^3 parity configuration in full: ICs, 6 BullFrog steps and P(k) on the 32^3 mesh
+    from oracle import mesh as omesh
+    c1 = nbody.Config(n_part=32, n_mesh=32, box=256.0, n_steps=6)
+    t1 = time.perf_counter()
+    P1, V1 = nbody.zeldovich_ic(c1, inputs.white_noise(32, 1))
+    P1, V1 = nbody.run(c1, P1, V1)
+    omesh.power_spectrum(omesh.density_contrast(np.mod(nbody.lattice(32, 256.0) + P1, 256.0), 32, 256.0, 2),
+                         256.0, 16)
+    dt1 = time.perf_counter() - t1
     return {"value": n ** 3 * 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"Zel'dovich ICs + 2 DKD steps at {n}^3 particles / {n}^3 mesh, L = {cfg.box:g} Mpc/h "
-                      f"(numpy FP64, single thread; {dt:.1f} s)"}
+                      f"(numpy FP64; {dt:.1f} s)",
+            "threads_note": "numpy's FFT and scatter-add run on one thread, so OMP_NUM_THREADS = 1 and = nproc "
+                            "time the same",
+            "host": host_cpu(), "parity_config_32cubed_full_s": dt1}
 
 
 def serving_benchmark(n_req, dev):
