@@ -35,6 +35,7 @@ class Config:
     time_var: str = "D"
     zero_corner: bool = True
     deconvolve: bool = False    # divide the force's density by the squared kernel (Table 4 `deconvolve`)
+    lpt_order: int = 1          # 1 = Zel'dovich ICs, 2 = 2LPT ICs (Table 4 `nlpt_order_ics`)
     growth: object = field(default=None, repr=False)
 
     @property
@@ -85,11 +86,50 @@ def ic_multipliers(cfg, pk=None):
     return [1j * kc * base for kc in (kx, ky, kz)]
 
 
+def lpt2_term(psi1, L):
+    """Second-order LPT displacement psi^(2) of Eq. LPT from the first-order one
+    (Sec. 2.2, Eqs. helmholtz / LPT_L_and_T / LPT_kernels at n = 2, D^n growth).
+
+    At n = 2 the transverse part vanishes (the factor n - 2s is zero for s = 1) and
+    the longitudinal part is L^(2) = -(3/7) mu_2L^(1,1) with
+    mu_2L^(1,1) = (1/2)(psi_i,i psi_j,j - psi_i,j psi_j,i) (sums over i, j); then
+    psi^(2) = Lap^-1 grad L^(2).  Derivatives and the inverse Laplacian use the
+    exact kernels i k and -k^2 (as the paper states for LPT).  Readings: the
+    products are formed on the n^3 grid without the 3/2-rule padding, and psi^(2)
+    is zeroed at k = 0 and on every Nyquist plane, like psi^(1).
+    psi1: (3, n^3) real; returns (3, n^3)."""
+    n = round(psi1.shape[1] ** (1.0 / 3.0))
+    k1 = mesh.wavenumbers(n, L)
+    kz, ky, kx = np.meshgrid(k1, k1, k1, indexing="ij")
+    kk = (kx, ky, kz)
+    ph = [np.fft.fftn(psi1[c].reshape(n, n, n)) for c in range(3)]
+    # d[i][j] = d psi_i / d q_j
+    d = [[np.fft.ifftn(1j * kk[j] * ph[i]).real for j in range(3)] for i in range(3)]
+    mu2 = np.zeros((n, n, n))
+    for i in range(3):
+        for j in range(3):
+            mu2 += 0.5 * (d[i][i] * d[j][j] - d[i][j] * d[j][i])
+    L2 = -3.0 / 7.0 * mu2
+    k2 = kx ** 2 + ky ** 2 + kz ** 2
+    nyq = np.arange(n) == n // 2
+    nz, ny, nx = np.meshgrid(nyq, nyq, nyq, indexing="ij")
+    keep = ~(nx | ny | nz) & (k2 > 0)
+    L2k = np.fft.fftn(L2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = np.where(keep, -1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
+    return np.stack([np.fft.ifftn(1j * kc * inv * L2k).real.reshape(-1) for kc in kk])
+
+
 def zeldovich_ic(cfg, w, pk=None):
-    """Psi0 = D(a_ini) psi1, V0 = psi1 from white noise w (shape (n,n,n), [z,y,x])."""
+    """Psi0 = D(a_ini) psi1, V0 = psi1 from white noise w (shape (n,n,n), [z,y,x]).
+    With cfg.lpt_order = 2 (2LPT, Eq. LPT truncated at n = 2 with D^n growth):
+    Psi0 = D psi1 + D^2 psi2 and V0 = dPsi/dD = psi1 + 2 D psi2."""
     ms = ic_multipliers(cfg, pk)
     psi1 = np.stack([mesh.apply_multiplier(w, m).reshape(-1) for m in ms])
     Dini = cfg.get_growth().D(cfg.a_ini)
+    if cfg.lpt_order == 2:
+        psi2 = lpt2_term(psi1, cfg.box)
+        return Dini * psi1 + Dini ** 2 * psi2, psi1 + 2.0 * Dini * psi2
     return Dini * psi1, psi1.copy()
 
 

@@ -71,6 +71,52 @@ def test_ic_zero_modes():
     np.testing.assert_allclose(Psi, cfg.get_growth().D(cfg.a_ini) * V, rtol=1e-15)
 
 
+def _lattice_fields(n, L):
+    q = np.arange(n) * (L / n)
+    qz, qy, qx = np.meshgrid(q, q, q, indexing="ij")
+    return qx, qy, qz
+
+
+def test_lpt2_vanishes_for_a_planar_wave():
+    # planar symmetry: psi_i,j is non-zero for i = j = x only, so mu_2L = 0 and psi^(2) = 0
+    n, L = 16, 100.0
+    qx, qy, qz = _lattice_fields(n, L)
+    k = 2 * math.pi * 2 / L
+    psi1 = np.stack([(3.0 * np.sin(k * qx)).reshape(-1), np.zeros(n ** 3), np.zeros(n ** 3)])
+    assert np.max(np.abs(nbody.lpt2_term(psi1, L))) < 1e-12
+
+
+def test_lpt2_crossed_waves_closed_form():
+    # psi1 = (A sin kx, B sin ky, 0): mu_2L = psi_x,x psi_y,y = A B k^2 cos kx cos ky,
+    # L2 = -(3/7) mu_2L, Lap^-1 L2 = (3/14) A B cos kx cos ky (|k|^2 = 2 k^2), so
+    # psi^(2) = grad of that = (3/14) A B k (-sin kx cos ky, -cos kx sin ky, 0)
+    n, L = 16, 100.0
+    qx, qy, qz = _lattice_fields(n, L)
+    k = 2 * math.pi * 3 / L
+    A, B = 2.0, -1.5
+    psi1 = np.stack([(A * np.sin(k * qx)).reshape(-1), (B * np.sin(k * qy)).reshape(-1), np.zeros(n ** 3)])
+    psi2 = nbody.lpt2_term(psi1, L)
+    c = 3.0 / 14.0 * A * B * k
+    np.testing.assert_allclose(psi2[0], (-c * np.sin(k * qx) * np.cos(k * qy)).reshape(-1), atol=1e-12)
+    np.testing.assert_allclose(psi2[1], (-c * np.cos(k * qx) * np.sin(k * qy)).reshape(-1), atol=1e-12)
+    assert np.max(np.abs(psi2[2])) < 1e-12
+
+
+def test_lpt2_ic_state():
+    # Psi0 = D psi1 + D^2 psi2 and V0 = psi1 + 2 D psi2 (the D-derivative of Psi)
+    cfg1 = nbody.Config(n_part=16, n_mesh=16, box=100.0)
+    cfg2 = nbody.Config(n_part=16, n_mesh=16, box=100.0, lpt_order=2)
+    w = np.random.default_rng(3).standard_normal((16, 16, 16))
+    P1, V1 = nbody.zeldovich_ic(cfg1, w)
+    P2, V2 = nbody.zeldovich_ic(cfg2, w)
+    D = cfg1.get_growth().D(cfg1.a_ini)
+    psi2 = nbody.lpt2_term(V1, 100.0)
+    np.testing.assert_allclose(P2, P1 + D ** 2 * psi2, atol=1e-14)
+    np.testing.assert_allclose(V2, V1 + 2 * D * psi2, atol=1e-14)
+    # second order is small at a = 0.02 but not zero
+    assert 0 < np.max(np.abs(P2 - P1)) < 1e-2 * np.max(np.abs(P1))
+
+
 def test_plane_wave_follows_zeldovich_solution():
     # A planar wave psi1 = A sin(2 pi q_x / L) e_x stays exactly Zel'dovich
     # (X = q + D psi1) until shell crossing; the PM run must follow it up to
