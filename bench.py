@@ -332,6 +332,35 @@ def scaleup_benchmark(dev, reps=3):
             "ms_per_pm_step": ms / 10, "particle_steps_per_s": n ** 3 * 10 / (ms / 1e3)}
 
 
+def lpt2_ic_benchmark(dev, reps=3):
+    """2LPT initial conditions for the 512^3 lattice (four spectral chains and
+    the source products) against the Zel'dovich ICs of the same handle size."""
+    import numpy as np
+    import torch
+    from paper_2510_05206_gb300 import PM, Config
+    n = WORKLOAD["n_part"]
+    out = {"workload": f"ic_{n}cubed"}
+    rng = np.random.default_rng(NOISE_SEED)
+    noise = torch.from_numpy(rng.standard_normal((1, n ** 3), dtype=np.float32)).to(dev)
+    for lpt in (1, 2):
+        pm = PM(Config(n_part=n, n_mesh=WORKLOAD["n_mesh"], box=WORKLOAD["box_mpc_h"], lpt_order=lpt), device=dev)
+        disp, vel = pm.new_state()
+        for _ in range(3):
+            pm.ic_zeldovich(noise, disp, vel)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(reps):
+            pm.ic_zeldovich(noise, disp, vel)
+        t1.record()
+        torch.cuda.synchronize()
+        out["ms_2lpt" if lpt == 2 else "ms_zeldovich"] = t0.elapsed_time(t1) / reps
+        pm.close()
+        del disp, vel
+    return out
+
+
 def deconvolve_benchmark(dev, reps=3):
     """The 512^3 workload with the force density deconvolved by the squared CIC
     kernel (N_g = N with deconvolution): ICs + 6 BullFrog steps."""
@@ -494,6 +523,7 @@ def main():
         line["adjoint"] = adjoint_benchmark(dev)
         line["scaleup"] = scaleup_benchmark(dev)
         line["deconvolve"] = deconvolve_benchmark(dev)
+        line["lpt2_ic"] = lpt2_ic_benchmark(dev)
     if not args.no_serving:
         line["serving"] = serving_benchmark(args.serve_requests, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

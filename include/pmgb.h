@@ -68,12 +68,15 @@ typedef struct pm_config {
                             assignment kernel, prod_c W^(k_c)^2 with W^ = sinc^p(k/2) of
                             Table 1 (Sec. 2.5, deconvolution of the interpolation kernel;
                             Table 4 `deconvolve`, default 0) */
+    int32_t lpt_order;   /* initial conditions: 1 = Zel'dovich (default, also 0), 2 = 2LPT
+                            (Sec. 2.2, Eq. LPT at n = 2 with D^n growth: Psi = D psi1 + D^2 psi2,
+                            V = psi1 + 2 D psi2; Table 4 `nlpt_order_ics`) */
 } pm_config;
 
 /* Fills *cfg with the defaults: CIC, no interlacing, 4th-order gradient, exact
  * Laplacian, Omega_m 0.3, h 0.7, n_s 0.96, sigma8 0.8, a 0.02 -> 1, 6 BullFrog
- * steps uniform in D, corner modes zeroed, no deconvolution, batch 1; n_part = n_mesh = 64,
- * L = 256. */
+ * steps uniform in D, corner modes zeroed, no deconvolution, Zel'dovich ICs, batch 1;
+ * n_part = n_mesh = 64, L = 256. */
 void pm_config_default(pm_config* cfg);
 
 /* Device bytes pm_init will allocate for cfg (for admission control). */
@@ -113,7 +116,12 @@ int pm_growth(const pm_handle* h, double a, double* out);
  * lattice order as the particles).  delta_lin(a=1)^ = noise^ sqrt(P(k) N / L^3),
  * P = BBKS spectrum normalised to sigma8; psi1^ = i k / k^2 delta_lin^ / D(1)
  * with k = 0, every Nyquist plane and (zero_corner) |k| > k_Ny set to zero;
- * vel = psi1, disp = D(a_ini) psi1. */
+ * vel = psi1, disp = D(a_ini) psi1.
+ * With cfg.lpt_order = 2 (2LPT, Sec. 2.2 Eqs. LPT / helmholtz / LPT_L_and_T at
+ * n = 2): psi2 = Lap^-1 grad L2, L2 = -(3/7) (1/2)(psi1_i,i psi1_j,j - psi1_i,j psi1_j,i),
+ * formed on the lattice grid with exact i k / -k^2 kernels, zero at k = 0 and on
+ * every Nyquist plane; disp = D psi1 + D^2 psi2, vel = psi1 + 2 D psi2 (D = D(a_ini)).
+ * 2LPT uses the force-mesh workspace as scratch (sized for it by pm_init). */
 int pm_ic_zeldovich(pm_handle* h, const float* noise, float* disp, float* vel);
 
 /* Same for one slot: noise, disp and vel point at that slot's data. */
@@ -177,7 +185,8 @@ int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adj_disp, float* ad
 /* Pullback through the Zel'dovich initial conditions: with psi1* = D(a_ini)
  * adj_disp + adj_vel, adj_noise = sum_c F_c^T psi1*_c (F_c: noise -> psi1_c);
  * dsigma8 (host [slot], may be NULL) = <adj_noise, noise> / sigma8, since psi1
- * is proportional to sigma8.  Synchronises the stream when dsigma8 != NULL. */
+ * is proportional to sigma8.  Synchronises the stream when dsigma8 != NULL.
+ * Zel'dovich ICs only (lpt_order = 2: PM_ERR_UNSUPPORTED). */
 int pm_ic_adjoint(pm_handle* h, const float* noise, const float* adj_disp, const float* adj_vel, float* adj_noise,
                   double* dsigma8);
 

@@ -7,6 +7,7 @@
 //            IC     (Zel'dovich displacement from white noise), 1 -> 3 spectra
 //            P(k)   (binned |delta_k|^2 with FP64 per-bin sums), 1 -> bins
 //            adjoint of the force operator (multiplier conj(m_c), summed), 3 -> 1
+//            2LPT (second derivatives of psi1 from w^; psi2 from its source), 1 -> 3
 // Transforms are unnormalised; normalisations are folded into the multipliers.
 #include "fft_core.cuh"
 #include "pm_kernels.h"
@@ -215,7 +216,8 @@ struct ZArgs {
     float kf;                 // 2 pi / L
 };
 
-enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5, Z_POT = 6, Z_POT_IL = 7, Z_DEC = 8 };
+enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5, Z_POT = 6, Z_POT_IL = 7,
+       Z_IC_D2 = 8, Z_IC_O2 = 9, Z_LPT2 = 10, Z_DEC = 16 };
 
 // MODE_DEC = mode | Z_DEC: the mode's multiplier also divides by the squared mass
 // assignment kernel (deconvolution tables in a.dec1), compiled only where used.
@@ -388,6 +390,30 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
                 }
                 return r;
             }
+            if (MODE == Z_IC_D2 || MODE == Z_IC_O2) {
+                // second derivatives of psi1 for the 2LPT source (Eq. LPT_kernels):
+                // psi1_i,j^ = i k_j psi1_i^ = -k_i k_j T(k^2) w^; D2: (xx, yy, zz), O2: (xy, xz, yz)
+                if (kx != n / 2 && y != n / 2 && e != n / 2) {
+                    const int m3[3] = {kx, my, mz};
+                    const int i0 = MODE == Z_IC_D2 ? axis : (axis == 2 ? 1 : 0);
+                    const int i1 = MODE == Z_IC_D2 ? axis : (axis == 0 ? 1 : 2);
+                    const float f = -a.kf * a.kf * (float)(m3[i0] * m3[i1]) *
+                                    __ldg(&a.ictab[kx * kx + my * my + mz * mz]);
+                    r = cscale(A(l, e), f);
+                }
+                return r;
+            }
+            if (MODE == Z_LPT2) {
+                // psi2_c^ = Lap^-1 grad_c L2^ = -i k_c L2^ / k^2 (scale = 1/M), zero at k = 0 and on
+                // every Nyquist plane
+                const int m2 = kx * kx + my * my + mz * mz;
+                if (m2 != 0 && kx != n / 2 && y != n / 2 && e != n / 2) {
+                    const int mc = axis == 0 ? kx : (axis == 1 ? my : mz);
+                    const float f = a.scale * (float)mc / (a.kf * (float)m2);
+                    r = cmul_i(cscale(A(l, e), f), -1);
+                }
+                return r;
+            }
             // g_c^ = -i D1(k_c) / K_lap(k) * scale * delta^   (k = 0 -> 0)
             const int bc = axis == 0 ? kx : (axis == 1 ? y : e);
             float2 d = A(l, e);
@@ -500,6 +526,9 @@ void launch_z(int mode, const ZArgs& a, int nslots, cudaStream_t st) {
             else launch_z_mode<LOG2N, Z_FORCE_IL>(a, nslots, st);
             break;
         case Z_IC: launch_z_mode<LOG2N, Z_IC>(a, nslots, st); break;
+        case Z_IC_D2: launch_z_mode<LOG2N, Z_IC_D2>(a, nslots, st); break;
+        case Z_IC_O2: launch_z_mode<LOG2N, Z_IC_O2>(a, nslots, st); break;
+        case Z_LPT2: launch_z_mode<LOG2N, Z_LPT2>(a, nslots, st); break;
         case Z_PK: launch_z_mode<LOG2N, Z_PK>(a, nslots, st); break;
         case Z_ADJ:
             if (dec) launch_z_mode<LOG2N, Z_ADJ | Z_DEC>(a, nslots, st);

@@ -1042,6 +1042,17 @@ __global__ void __launch_bounds__(256) k_dot(const float* __restrict__ a, const 
     if (threadIdx.x == 0) atomicAdd(&out[slot], red[0]);
 }
 
+// 2LPT source from three real fields per slot (see pm_lpt2_source)
+__global__ void k_lpt2_source(int pass, const float* __restrict__ t, float* __restrict__ mu, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* ts = t + blockIdx.y * 3 * n;
+    float* m = mu + blockIdx.y * n;
+    const float a = ts[i], b = ts[n + i], c = ts[2 * n + i];
+    if (pass == 0) m[i] = a * b + a * c + b * c;
+    else m[i] = (-3.f / 7.f) * (m[i] - (a * a + b * b + c * c));
+}
+
 // out = a * x + b * y elementwise
 __global__ void k_axpby(float* __restrict__ out, const float* __restrict__ x, const float* __restrict__ y, float a,
                         float b, long long n) {
@@ -1203,5 +1214,11 @@ int pm_div_stencil(int grad_order, int log2n, float inv_h, const float* s3, long
     else if (grad_order == 4) k_div_stencil<4><<<grid, 256, 0, st>>>(log2n, inv_h, s3, s_stride, div, d_stride);
     else if (grad_order == 6) k_div_stencil<6><<<grid, 256, 0, st>>>(log2n, inv_h, s3, s_stride, div, d_stride);
     else return -1;
+    return 0;
+}
+
+int pm_lpt2_source(int pass, const float* t, float* mu, long long n, int nslots, cudaStream_t st) {
+    dim3 grid((unsigned)((n + 255) / 256), nslots);
+    k_lpt2_source<<<grid, 256, 0, st>>>(pass, t, mu, n);
     return 0;
 }

@@ -168,6 +168,7 @@ int validate(const pm_config* c, std::string& why) {
     if (c->order != 2 && c->order != 3) return bad("order must be 2 (CIC) or 3 (TSC)");
     if (c->interlace != 0 && c->interlace != 1) return bad("interlace must be 0 or 1");
     if (c->deconvolve != 0 && c->deconvolve != 1) return bad("deconvolve must be 0 or 1");
+    if (c->lpt_order < 0 || c->lpt_order > 2) return bad("lpt_order must be 0, 1 (Zel'dovich) or 2 (2LPT)");
     for (int o : {c->grad_order, c->lap_order})
         if (o != 0 && o != 2 && o != 4 && o != 6) return bad("grad_order / lap_order must be 0, 2, 4 or 6");
     if (!(c->omega_m > 0 && c->omega_m <= 1)) return bad("omega_m must be in (0, 1]");
@@ -193,7 +194,9 @@ size_t workspace_bytes(const pm_config* c) {
     size_t b = 0;
     b += (size_t)c->batch * ngrids * std::max(mesh_elems(ng), mesh_elems(npk)) * 4;
     b += (size_t)c->batch * ncomp * spec_elems(nmax) * 8;
-    b += (size_t)c->batch * ngrids * mesh_elems(ng) * 16;
+    // force meshes (float4); 2LPT ICs also use them for four real lattice fields per slot
+    b += (size_t)c->batch * std::max((long long)ngrids * mesh_elems(ng),
+                                     c->lpt_order == 2 ? (long long)mesh_elems(np) : 0ll) * 16;
     b += (size_t)(3 * (np / 2) * (np / 2) + 1) * 4 + 8 * 1024 * 8 * 2 + (size_t)ng * 8;
     b += (size_t)(c->n_steps + c->batch + 1) * sizeof(SlotCoef);
     return b;
@@ -369,10 +372,59 @@ int bintab_for(pm_handle* h, int n, int nbins, const pm_handle::BinTable** out) 
     return PM_OK;
 }
 
+// One IC spectral chain: forward transform of `src` (slot stride src_stride), the z
+// pass `mode` producing three spectra, inverse transforms into three real fields
+// per slot at dst (slot stride 3 Np) -- or, for the Zel'dovich pass (dst NULL),
+// into vel and D disp.
+void ic_chain(pm_handle* h, const float* src, long long src_stride, int mode, float scale, float* dst, float* disp,
+              float* vel, int nslots) {
+    const int n = h->np, l2 = ilog2i(n);
+    const long long S = spec_elems(n), SS = 3 * S;
+    cudaStream_t st = h->stream;
+    pm_fft_r2c_x(l2, src, src_stride, h->spec, SS, nslots, h->d_tw[l2], st);
+    pm_fft_y(l2, h->spec, SS, nslots, -1, h->d_tw[l2], st);
+    PmZPass z{};
+    z.in[0] = h->spec;
+    for (int c = 0; c < 3; ++c) z.out[c] = h->spec + c * S;
+    z.slot_stride = SS;
+    z.tw = h->d_tw[l2];
+    z.ictab = h->d_ictab;
+    z.kf = (float)(2.0 * M_PI / h->cfg.box);
+    z.scale = scale;
+    pm_fft_z(l2, mode, z, nslots, st);
+    pm_fft_y(l2, h->spec, S, 3 * nslots, 1, h->d_tw[l2], st);
+    if (dst)
+        pm_fft_c2r_x(l2, h->spec, S, dst, h->Np(), nullptr, 0, 0.f, 3 * nslots, h->d_tw[l2], st);
+    else
+        pm_fft_c2r_x(l2, h->spec, S, vel, h->Np(), disp, h->Np(), (float)h->growth->D(h->cfg.a_ini), 3 * nslots,
+                     h->d_tw[l2], st);
+}
+
 int ic_impl(pm_handle* h, const float* noise, float* disp, float* vel, int nslots) {
     const int n = h->np, l2 = ilog2i(n);
     const long long S = spec_elems(n), SS = 3 * S;
     cudaStream_t st = h->stream;
+    if (h->cfg.lpt_order == 2) {
+        // 2LPT (Eq. LPT at n = 2): the source L2 = -(3/7) mu_2L from the six second
+        // derivatives of psi1 (three at a time into lattice fields t; mu after them,
+        // both in the force-mesh buffer), psi2 = Lap^-1 grad L2 into t, then the
+        // Zel'dovich state and Psi += D^2 psi2, V += 2 D psi2
+        const long long Np = h->Np();
+        float* t = reinterpret_cast<float*>(h->force);
+        float* mu = t + 3 * Np * nslots;
+        h->phase(7, 24);
+        ic_chain(h, noise, Np, PM_Z_IC_D2, 0.f, t, nullptr, nullptr, nslots);
+        pm_lpt2_source(0, t, mu, Np, nslots, st);
+        ic_chain(h, noise, Np, PM_Z_IC_O2, 0.f, t, nullptr, nullptr, nslots);
+        pm_lpt2_source(1, t, mu, Np, nslots, st);
+        ic_chain(h, mu, Np, PM_Z_LPT2, (float)(1.0 / (double)Np), t, nullptr, nullptr, nslots);
+        ic_chain(h, noise, Np, PM_Z_IC, 0.f, nullptr, disp, vel, nslots);
+        const double D = h->growth->D(h->cfg.a_ini);
+        pm_axpby(disp, disp, t, 1.f, (float)(D * D), 3 * Np * nslots, st);
+        pm_axpby(vel, vel, t, 1.f, (float)(2.0 * D), 3 * Np * nslots, st);
+        h->phase_end();
+        return h->check_launch("2lpt ic");
+    }
     h->phase(7, 5);
     pm_fft_r2c_x(l2, noise, h->Np(), h->spec, SS, nslots, h->d_tw[l2], st);
     pm_fft_y(l2, h->spec, SS, nslots, -1, h->d_tw[l2], st);
@@ -418,6 +470,7 @@ void pm_config_default(pm_config* c) {
     c->batch = 1;
     c->pk_mesh_max = 0;
     c->deconvolve = 0;
+    c->lpt_order = 1;
 }
 
 int pm_workspace_bytes(const pm_config* cfg, size_t* bytes) {
@@ -458,7 +511,8 @@ int pm_init(const pm_config* cfg, void* stream, pm_handle** out) {
     const int B = h->B;
     if ((rc = dalloc(h.get(), &h->rho, (size_t)B * h->rho_slot(), "density"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->spec, (size_t)B * h->spec_slot(), "spectra"))) return bail(rc);
-    if ((rc = dalloc(h.get(), &h->force, (size_t)B * h->ngrids * h->Mg(), "force meshes"))) return bail(rc);
+    const long long f4 = std::max((long long)h->ngrids * h->Mg(), cfg->lpt_order == 2 ? (long long)h->Np() : 0ll);
+    if ((rc = dalloc(h.get(), &h->force, (size_t)B * f4, "force meshes"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->d_table, (size_t)cfg->n_steps, "step table"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->d_slots, (size_t)B, "slot table"))) return bail(rc);
     if ((rc = dalloc(h.get(), &h->d_unit, 1, "unit coef"))) return bail(rc);
@@ -877,6 +931,8 @@ int pm_ic_adjoint(pm_handle* h, const float* noise, const float* adisp, const fl
                   double* dsigma8) {
     if (!h) return PM_ERR_ARG;
     if (!noise || !adisp || !avel || !anoise) return h->fail(PM_ERR_ARG, "pm_ic_adjoint: NULL buffer");
+    if (h->cfg.lpt_order == 2)
+        return h->fail(PM_ERR_UNSUPPORTED, "pm_ic_adjoint: the pullback is implemented for Zel'dovich ICs only");
     int rc;
     if ((rc = adj_alloc(h))) return rc;
     cudaStream_t st = h->stream;

@@ -22,7 +22,7 @@ struct PmZPass {
 };
 
 enum { PM_Z_FORCE = 0, PM_Z_FORCE_IL = 1, PM_Z_IC = 2, PM_Z_PK = 3, PM_Z_ADJ = 4, PM_Z_IC_ADJ = 5, PM_Z_POT = 6,
-       PM_Z_POT_IL = 7 };
+       PM_Z_POT_IL = 7, PM_Z_IC_D2 = 8, PM_Z_IC_O2 = 9, PM_Z_LPT2 = 10 };
 
 // clear_in != 0: the input rows are zeroed after they are read (a density mesh
 // consumed here is then ready for the next deposit without a separate memset)
@@ -81,3 +81,9 @@ int pm_adj_gather_grad(int order, int finish, const PmGeom& g, float* disp, cons
                        cudaStream_t st);
 int pm_dot(const float* a, const float* b, long long n, double* out, int nslots, cudaStream_t st);
 int pm_axpby(float* out, const float* x, const float* y, float a, float b, long long n, cudaStream_t st);
+
+// 2LPT source (Eq. LPT_kernels at n = 2) from three real fields t0..t2 of n elements
+// per slot (slot stride 3n, mu slot stride n):
+// pass 0 (diagonal psi_x,x, psi_y,y, psi_z,z): mu = t0 t1 + t0 t2 + t1 t2;
+// pass 1 (off-diagonal psi_x,y, psi_x,z, psi_y,z): mu = -(3/7) (mu - t0^2 - t1^2 - t2^2) = L^(2).
+int pm_lpt2_source(int pass, const float* t, float* mu, long long n, int nslots, cudaStream_t st);

@@ -32,6 +32,7 @@ class Config:
     batch: int = 1
     pk_mesh_max: int = 0
     deconvolve: int = 0         # divide the force density by the squared kernel (Table 1 W^)
+    lpt_order: int = 1          # initial conditions: 1 = Zel'dovich, 2 = 2LPT
 
     def to_c(self):
         c = _lib.PmConfig()

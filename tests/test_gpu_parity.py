@@ -126,6 +126,24 @@ def test_zeldovich_ic(n, corner):
     assert _rel_max(_np(disp)[0], P0) < 2e-5
 
 
+@pytest.mark.parametrize("n", [32, 64])
+def test_lpt2_ic(n):
+    # 2LPT ICs against the oracle; the second-order part alone (2LPT minus Zel'dovich
+    # velocities = 2 D psi2) at a_ini = 0.1, where it is large enough to be resolved
+    # by the float32 difference
+    L = 256.0
+    kw = dict(n_part=n, n_mesh=n, box=L, a_ini=0.1)
+    w = inputs.white_noise(n, seed=4)
+    d1, v1 = PM(Config(**kw), device=DEV).ic_zeldovich(_t(w.reshape(1, -1)))
+    d2, v2 = PM(Config(lpt_order=2, **kw), device=DEV).ic_zeldovich(_t(w.reshape(1, -1)))
+    P1, V1 = nbody.zeldovich_ic(nbody.Config(**kw), w)
+    P2, V2 = nbody.zeldovich_ic(nbody.Config(lpt_order=2, **kw), w)
+    assert _rel_max(_np(d2)[0], P2) < 2e-5
+    assert _rel_max(_np(v2)[0], V2) < 2e-5
+    assert _rel_max(_np(v2)[0] - _np(v1)[0], V2 - V1) < 2e-3
+    assert _rel_max(_np(d2)[0] - _np(d1)[0], P2 - P1) < 2e-3
+
+
 def _run_pair(cfg_kw, seed, n_bins=None):
     cfg = Config(**cfg_kw)
     pm = PM(cfg, device=DEV)
@@ -136,7 +154,7 @@ def _run_pair(cfg_kw, seed, n_bins=None):
                interlace=bool(cfg.interlace), grad_order=cfg.grad_order, lap_order=cfg.lap_order,
                n_steps=cfg.n_steps, a_ini=cfg.a_ini, a_end=cfg.a_end,
                stepper=["bullfrog", "fastpm"][cfg.stepper], time_var=["D", "a"][cfg.time_var],
-               deconvolve=bool(cfg.deconvolve))
+               deconvolve=bool(cfg.deconvolve), lpt_order=max(cfg.lpt_order, 1))
     ocfg = nbody.Config(**okw)
     P0, V0 = nbody.zeldovich_ic(ocfg, w)
     P1, V1 = nbody.run(ocfg, P0, V0)
@@ -172,6 +190,8 @@ def test_full_run_config1_parity():
     dict(n_part=32, n_mesh=32, box=150.0, order=2, interlace=1, n_steps=3, grad_order=0),   # 6 inverse FFTs
     dict(n_part=32, n_mesh=32, box=256.0, order=2, n_steps=6, deconvolve=1),                 # option (ii): N_g = N + deconv.
     dict(n_part=32, n_mesh=32, box=200.0, order=3, n_steps=4, deconvolve=1, interlace=1),
+    dict(n_part=32, n_mesh=32, box=256.0, order=2, n_steps=6, lpt_order=2),                 # 2LPT ICs
+    dict(n_part=64, n_mesh=32, box=256.0, order=2, n_steps=4, lpt_order=2),                 # mesh smaller than lattice
 ])
 def test_full_run_variants_parity(kw):
     pm, disp, vel, P1, V1 = _run_pair(kw, seed=2)
