@@ -14,10 +14,12 @@ It restates, step by step and in double precision, what the paper
   kick coefficients (Sec. 2.4), the BBKS linear spectrum normalised to sigma8.
 * ``mesh``       - mass-assignment kernels (Table 1), scatter / gather and
   their position derivatives (App. C), finite-difference gradient and
-  Laplacian kernels (Table 2), the Poisson force field (Sec. 2.5, Eq. poisson),
+  Laplacian kernels (Table 2), the Poisson force field (Sec. 2.5, Eq. poisson)
+  with optional deconvolution by the squared kernel (Sec. 2.5, Table 1),
   interlacing, and the binned power spectrum.
-* ``nbody``      - Zel'dovich initial conditions (Sec. 2.2), the DKD stepper
-  (Eq. dkd), full runs, and the adjoint method (Sec. 2.7, Table 5, App. C).
+* ``nbody``      - Zel'dovich and 2LPT initial conditions (Sec. 2.2, Eqs. LPT,
+  helmholtz, LPT_L_and_T), the DKD stepper (Eq. dkd), full runs, and the
+  adjoint method (Sec. 2.7, Table 5, App. C).
 
 Readings of places where the paper is silent, ambiguous or garbled are stated
 in the docstring of the function that takes them.
