@@ -48,7 +48,7 @@ typedef struct pm_config {
     int32_t n_part;      /* particles per dimension, N = n_part^3 */
     int32_t n_mesh;      /* PM mesh cells per dimension (Table 4 res_pm) */
     double box;          /* L [Mpc/h] */
-    int32_t order;       /* mass-assignment kernel (Table 1): 2 = CIC, 3 = TSC */
+    int32_t order;       /* mass-assignment kernel (Table 1): 2 = CIC, 3 = TSC, 4 = PCS */
     int32_t interlace;   /* 0, or 1 = one extra grid shifted by half a cell (Sec. 2.8) */
     int32_t grad_order;  /* gradient kernel (Table 2): 0 = i k, 2/4/6 = finite difference; default 4 */
     int32_t lap_order;   /* Laplacian kernel (Table 2): 0 = -k^2, 2/4/6; default 0 */

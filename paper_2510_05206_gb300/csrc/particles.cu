@@ -13,8 +13,8 @@ namespace {
 // s cells, for a mesh 2^dshift times finer than the lattice (dshift may be < 0).
 struct AxisTaps {
     int c;       // first tap cell (unwrapped)
-    float w[3];  // weights of taps c, c+1 (CIC) or c, c+1, c+2 (TSC)
-    float dw[3]; // d w / d u (u = position in cells), one-sided at CIC kinks as the floor gives
+    float w[4];  // weights of taps c, c+1 (CIC), c .. c+2 (TSC) or c .. c+3 (PCS)
+    float dw[4]; // d w / d u (u = position in cells), one-sided at CIC kinks as the floor gives
 };
 
 template <int ORDER>
@@ -42,6 +42,21 @@ __device__ __forceinline__ AxisTaps axis_taps(int il, int dshift, float s) {
         a.dw[0] = -1.f;
         a.dw[1] = 1.f;
         a.dw[2] = 0.f;
+    } else if (ORDER == 4) {
+        // PCS (Table 1, cubic B-spline): cells floor(t)-1 .. floor(t)+2 at distances
+        // 1+d, d, 1-d, 2-d (d = t - floor(t)); dw/du = -W'(x) at x = cell - u
+        const float fl = floorf(t);
+        const float d = t - fl, e = 1.f - d;
+        a.c = base + (int)fl - 1;
+        a.w[0] = e * e * e * (1.f / 6.f);
+        a.w[1] = (4.f - 6.f * d * d + 3.f * d * d * d) * (1.f / 6.f);
+        a.w[2] = (4.f - 6.f * e * e + 3.f * e * e * e) * (1.f / 6.f);
+        a.w[3] = d * d * d * (1.f / 6.f);
+        a.dw[0] = -0.5f * e * e;
+        a.dw[1] = -2.f * d + 1.5f * d * d;
+        a.dw[2] = 2.f * e - 1.5f * e * e;
+        a.dw[3] = 0.5f * d * d;
+        return a;
     } else {
         // TSC (Table 1): nearest node i0 = floor(t + 1/2), d = t - i0 in [-1/2, 1/2)
         const float fl = floorf(t + 0.5f);
@@ -192,14 +207,15 @@ constexpr float DEP_UNFIX = 1.f / 1048576.f;
 
 template <int ORDER>
 struct DepWindow {
-    static constexpr int LO = ORDER == 3 ? 1 : 0;   // taps below the base cell
+    static constexpr int LO = ORDER >= 3 ? 1 : 0;   // taps below the base cell
+    static constexpr int HALO = ORDER == 4 ? 2 : DEP_HALO;   // PCS: 4 taps leave room for 2
     static constexpr int WX = 44;                   // 32 + 2 halo + ORDER - 1 + alignment slack, rounded to 4
     static constexpr int WY = 16;                   // 8 + 2 halo + ORDER - 1, rounded up
     static constexpr int WZ = 16;
     static constexpr int QX = WX / 4;               // 16-byte groups per window row
     static constexpr int CELLS = WX * WY * WZ;
     static_assert(QX <= 16 && WY == 16, "flush maps 16 lanes per row, 16 rows per plane");
-    static_assert(32 + 2 * DEP_HALO + ORDER - 1 + 3 <= WX && 8 + 2 * DEP_HALO + ORDER - 1 <= WY, "window");
+    static_assert(32 + 2 * HALO + ORDER - 1 + 3 <= WX && 8 + 2 * HALO + ORDER - 1 <= WY, "window");
 };
 
 __device__ __forceinline__ void red_v4(float* p, float4 v) {
@@ -319,9 +335,9 @@ __global__ void __launch_bounds__(256, 4) k_deposit_tiled(PmGeom g, const float*
             mean[c] = ((u.x + u.y) + (u.z + u.w) + ((w.x + w.y) + (w.z + w.w))) *
                       (1.f / (TG::TXP * TG::TYP * TG::TZP));
         }
-        const int ox = (T.ix0 * R + __float2int_rn(mean[0]) - DEP_HALO - Win::LO) & ~3;
-        const int oy = T.iy0 * R + __float2int_rn(mean[1]) - DEP_HALO - Win::LO;
-        const int oz = T.iz0 * R + __float2int_rn(mean[2]) - DEP_HALO - Win::LO;
+        const int ox = (T.ix0 * R + __float2int_rn(mean[0]) - Win::HALO - Win::LO) & ~3;
+        const int oy = T.iy0 * R + __float2int_rn(mean[1]) - Win::HALO - Win::LO;
+        const int oz = T.iz0 * R + __float2int_rn(mean[2]) - Win::HALO - Win::LO;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
             const AxisTaps ax = axis_taps<ORDER>(T.ix, DS, sx[p]);
@@ -1067,7 +1083,7 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
     const long long N = 1ll << (3 * g.log2np);
     const int R = 1 << (g.log2ng - g.log2np > 0 ? g.log2ng - g.log2np : 0);
     const bool tiled = (g.log2ng - g.log2np == 0 && g.log2np >= 5) || (g.log2ng - g.log2np == 1 && g.log2np >= 4);
-    if (tiled && (order == 2 || order == 3)) {
+    if (tiled && order >= 2 && order <= 4) {
         const int np = 1 << g.log2np;
         const unsigned ntiles = (unsigned)((long long)(np / (32 / R)) * (np / (8 / R)) * (np / (8 / R)));
 #define PM_DT(O, RR)                                                                                        \
@@ -1090,8 +1106,10 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
     }
         if (order == 2 && R == 1) PM_DT(2, 1)
         else if (order == 2) PM_DT(2, 2)
-        else if (R == 1) PM_DT(3, 1)
-        else PM_DT(3, 2)
+        else if (order == 3 && R == 1) PM_DT(3, 1)
+        else if (order == 3) PM_DT(3, 2)
+        else if (R == 1) PM_DT(4, 1)
+        else PM_DT(4, 2)
 #undef PM_DT
         return 0;
     }
@@ -1100,6 +1118,8 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
         k_deposit<2><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho);
     else if (order == 3)
         k_deposit<3><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho);
+    else if (order == 4)
+        k_deposit<4><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho);
     else
         return -1;
     return 0;
@@ -1120,6 +1140,8 @@ int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float
     else if (order == 2 && interlace) PM_IK(2, 1);
     else if (order == 3 && !interlace) PM_IK(3, 0);
     else if (order == 3 && interlace) PM_IK(3, 1);
+    else if (order == 4 && !interlace) PM_IK(4, 0);
+    else if (order == 4 && interlace) PM_IK(4, 1);
     else return -1;
 #undef PM_IK
     return 0;
@@ -1135,6 +1157,8 @@ int pm_interp(int order, int interlace, const PmGeom& g, const float* disp, cons
     else if (order == 2 && interlace) PM_I(2, 1);
     else if (order == 3 && !interlace) PM_I(3, 0);
     else if (order == 3 && interlace) PM_I(3, 1);
+    else if (order == 4 && !interlace) PM_I(4, 0);
+    else if (order == 4 && interlace) PM_I(4, 1);
     else return -1;
 #undef PM_I
     return 0;
@@ -1146,6 +1170,7 @@ int pm_adj_drift_deposit(int order, const PmGeom& g, float* disp, const float* v
     dim3 grid((unsigned)((N + 255) / 256), nslots);
     if (order == 2) k_adj_drift_deposit<2><<<grid, 256, 0, st>>>(g, disp, vel, adisp, avel, coef, cstride, rho);
     else if (order == 3) k_adj_drift_deposit<3><<<grid, 256, 0, st>>>(g, disp, vel, adisp, avel, coef, cstride, rho);
+    else if (order == 4) k_adj_drift_deposit<4><<<grid, 256, 0, st>>>(g, disp, vel, adisp, avel, coef, cstride, rho);
     else return -1;
     return 0;
 }
@@ -1156,6 +1181,7 @@ int pm_adj_interp(int order, const PmGeom& g, const float* disp, float* vel, flo
     dim3 grid((unsigned)((N + 255) / 256), nslots);
     if (order == 2) k_adj_interp<2><<<grid, 256, 0, st>>>(g, disp, vel, adisp, avel, coef, cstride, force, s3);
     else if (order == 3) k_adj_interp<3><<<grid, 256, 0, st>>>(g, disp, vel, adisp, avel, coef, cstride, force, s3);
+    else if (order == 4) k_adj_interp<4><<<grid, 256, 0, st>>>(g, disp, vel, adisp, avel, coef, cstride, force, s3);
     else return -1;
     return 0;
 }
@@ -1170,6 +1196,8 @@ int pm_adj_gather_grad(int order, int finish, const PmGeom& g, float* disp, cons
     else if (order == 2) PM_AG(2, 0);
     else if (order == 3 && finish) PM_AG(3, 1);
     else if (order == 3) PM_AG(3, 0);
+    else if (order == 4 && finish) PM_AG(4, 1);
+    else if (order == 4) PM_AG(4, 0);
     else return -1;
 #undef PM_AG
     return 0;

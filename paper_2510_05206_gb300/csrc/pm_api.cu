@@ -165,7 +165,7 @@ int validate(const pm_config* c, std::string& why) {
     if (!pow2_in_range(c->n_mesh)) return bad("n_mesh must be a power of two in [16, 1024]");
     if (c->pk_mesh_max && !pow2_in_range(c->pk_mesh_max)) return bad("pk_mesh_max must be 0 or a power of two in [16, 1024]");
     if (!(c->box > 0)) return bad("box must be > 0");
-    if (c->order != 2 && c->order != 3) return bad("order must be 2 (CIC) or 3 (TSC)");
+    if (c->order < 2 || c->order > 4) return bad("order must be 2 (CIC), 3 (TSC) or 4 (PCS)");
     if (c->interlace != 0 && c->interlace != 1) return bad("interlace must be 0 or 1");
     if (c->deconvolve != 0 && c->deconvolve != 1) return bad("deconvolve must be 0 or 1");
     if (c->lpt_order < 0 || c->lpt_order > 2) return bad("lpt_order must be 0, 1 (Zel'dovich) or 2 (2LPT)");
@@ -821,7 +821,7 @@ int pm_density(pm_handle* h, const float* disp, int32_t n, int32_t order, float*
     if (!h) return PM_ERR_ARG;
     if (!disp || !delta) return h->fail(PM_ERR_ARG, "pm_density: NULL buffer");
     if (!pow2_in_range(n)) return h->fail(PM_ERR_ARG, "mesh %d must be a power of two in [16, 1024]", n);
-    if (order != 2 && order != 3) return h->fail(PM_ERR_ARG, "order must be 2 or 3");
+    if (order < 2 || order > 4) return h->fail(PM_ERR_ARG, "order must be 2, 3 or 4");
     const long long M = mesh_elems(n);
     cudaStream_t st = h->stream;
     cudaMemsetAsync(delta, 0, sizeof(float) * M * h->B, st);
@@ -972,7 +972,7 @@ int pm_density_vjp(pm_handle* h, const float* disp, int32_t n, int32_t order, co
     if (!h) return PM_ERR_ARG;
     if (!disp || !ddelta || !adisp) return h->fail(PM_ERR_ARG, "pm_density_vjp: NULL buffer");
     if (!pow2_in_range(n)) return h->fail(PM_ERR_ARG, "mesh %d must be a power of two in [16, 1024]", n);
-    if (order != 2 && order != 3) return h->fail(PM_ERR_ARG, "order must be 2 or 3");
+    if (order < 2 || order > 4) return h->fail(PM_ERR_ARG, "order must be 2, 3 or 4");
     const long long M = mesh_elems(n);
     // delta = (M/N) sum_i W(r_j - X_i) - 1  =>  X*_i = (M/N) sum_j delta*_j d/dX_i W(r_j - X_i)
     pm_adj_gather_grad(order, 0, geom(h, n, M), const_cast<float*>(disp), nullptr, adisp, nullptr, nullptr, 0, ddelta,

@@ -35,7 +35,8 @@ def _rel_max(got, ref):
     return np.max(np.abs(got - ref)) / np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("n_part,n_mesh,order", [(32, 32, 2), (32, 64, 2), (32, 32, 3), (64, 32, 3), (16, 64, 2)])
+@pytest.mark.parametrize("n_part,n_mesh,order", [(32, 32, 2), (32, 64, 2), (32, 32, 3), (64, 32, 3), (16, 64, 2),
+                                                 (32, 32, 4), (32, 64, 4)])
 def test_density_deposit(n_part, n_mesh, order):
     L = 100.0
     pm = PM(Config(n_part=n_part, n_mesh=n_mesh, box=L, order=order), device=DEV)
@@ -48,7 +49,7 @@ def test_density_deposit(n_part, n_mesh, order):
     assert abs(delta.sum()) < 1e-4 * n_mesh ** 3 ** 0.5 + 1e-3
 
 
-@pytest.mark.parametrize("n_part,n_mesh,order", [(32, 32, 2), (64, 64, 2), (32, 32, 3), (32, 64, 2), (32, 64, 3)])
+@pytest.mark.parametrize("n_part,n_mesh,order", [(32, 32, 2), (64, 64, 2), (32, 32, 3), (32, 64, 2), (32, 64, 3), (32, 32, 4), (32, 64, 4)])
 def test_density_deposit_structured(n_part, n_mesh, order):
     # tile-window paths of the deposit: jittered columns, collapsed columns (many
     # particles per cell) and particles far outside their tile's window
@@ -100,7 +101,7 @@ def test_force_mesh(n, grad, lap, order, dec):
         assert _rel_max(g[c], ref[c]) < 2e-5, c
 
 
-@pytest.mark.parametrize("n_part,n_mesh,order", [(32, 32, 2), (32, 64, 3), (64, 32, 2)])
+@pytest.mark.parametrize("n_part,n_mesh,order", [(32, 32, 2), (32, 64, 3), (64, 32, 2), (32, 32, 4)])
 def test_interp(n_part, n_mesh, order):
     L = 80.0
     pm = PM(Config(n_part=n_part, n_mesh=n_mesh, box=L, order=order), device=DEV)
@@ -191,6 +192,8 @@ def test_full_run_config1_parity():
     dict(n_part=32, n_mesh=32, box=256.0, order=2, n_steps=6, deconvolve=1),                 # option (ii): N_g = N + deconv.
     dict(n_part=32, n_mesh=32, box=200.0, order=3, n_steps=4, deconvolve=1, interlace=1),
     dict(n_part=32, n_mesh=32, box=256.0, order=2, n_steps=6, lpt_order=2),                 # 2LPT ICs
+    dict(n_part=32, n_mesh=32, box=256.0, order=4, n_steps=4, deconvolve=1),                 # PCS + deconvolution
+    dict(n_part=32, n_mesh=64, box=200.0, order=4, n_steps=3, interlace=1),                  # PCS, interlaced
     dict(n_part=64, n_mesh=32, box=256.0, order=2, n_steps=4, lpt_order=2),                 # mesh smaller than lattice
 ])
 def test_full_run_variants_parity(kw):
