@@ -144,6 +144,16 @@ def gather_grad(mesh, X, L, order, shift=0.0):
     return g
 
 
+def scatter_dot_grad(X, T, n, L, order, shift=0.0):
+    """Tangent of scatter(X, 1) along position tangents T (3, N):
+    rho'_j = sum_i sum_d T_di d/dX_di W(r_j - X_i)  (forward mode of App. C's scatter)."""
+    M = n ** 3
+    rho = np.zeros(M)
+    for idx, _, grad in _tap_products(X, n, L, order, shift):
+        rho += np.bincount(idx, weights=T[0] * grad[0] + T[1] * grad[1] + T[2] * grad[2], minlength=M)
+    return rho.reshape(n, n, n)
+
+
 def density_contrast(X, n, L, order, shift=0.0):
     """delta_j = rho_j M / N - 1 with unit particle masses (Sec. 2.5, Fourier density with PM)."""
     N = X.shape[1]

@@ -200,6 +200,78 @@ def run(cfg, Psi, V, table=None, force_fn=None, n_steps=None):
 
 
 # --------------------------------------------------------------------------
+# forward mode (tangents; the JVP counterpart of App. C)
+# --------------------------------------------------------------------------
+
+def accel_jvp(cfg, Psi_h, q, Dh, T):
+    """(grad_X A) . T for A = g(X)/Dh^2 (non-interlaced PM): returns (3, N).
+
+    A_kc = Dh^-2 sum_j g_cj W(r_j - X_k), g_c = F_c delta, delta = (M/N) scatter(1) - 1.
+    Two contributions: the gather's dependence on the positions,
+    sum_d T_dk sum_j g_cj dW/dX_dk; and on the mesh, the gather of
+    g'_c = F_c delta', delta' = (M/N) scatter_dot_grad(T)."""
+    if cfg.interlace:
+        raise NotImplementedError("forward mode is defined for a single grid")
+    n, L = cfg.n_mesh, cfg.box
+    N = Psi_h.shape[1]
+    X = np.mod(q + Psi_h, L)
+    delta = mesh.density_contrast(X, n, L, cfg.order)
+    ms = mesh.force_multipliers(n, L, cfg.grad_order, cfg.lap_order, deconvolve_order=cfg.deconv_order)
+    g = [mesh.apply_multiplier(delta, m) for m in ms]
+    ddelta = (n ** 3 / N) * mesh.scatter_dot_grad(X, T, n, L, cfg.order)
+    out = np.zeros((3, N))
+    for c in range(3):
+        gg = mesh.gather_grad(g[c], X, L, cfg.order)
+        out[c] = (T * gg).sum(axis=0) + mesh.gather(mesh.apply_multiplier(ddelta, ms[c]), X, L, cfg.order)
+    return out / Dh ** 2
+
+
+def step_jvp(cfg, Psi, V, Pt, Vt, coef, q):
+    """One DKD step with its tangent: (Psi, V, Psi', V') -> the next state and tangent."""
+    tau1, tau2, alpha, beta, Dh = coef[:5]
+    Ph, Pht = Psi + tau1 * V, Pt + tau1 * Vt
+    A = accel(cfg, Ph, q, Dh)
+    At = accel_jvp(cfg, Ph, q, Dh, Pht)
+    V2, V2t = alpha * V + beta * A, alpha * Vt + beta * At
+    return Ph + tau2 * V2, V2, Pht + tau2 * V2t, V2t
+
+
+def run_jvp(cfg, Psi, V, Pt, Vt, table=None):
+    table = cosmology.step_table(cfg.get_growth(), cfg.a_ini, cfg.a_end, cfg.n_steps,
+                                 cfg.stepper, cfg.time_var) if table is None else table
+    q = lattice(cfg.n_part, cfg.box)
+    for row in table:
+        Psi, V, Pt, Vt = step_jvp(cfg, Psi, V, Pt, Vt, row, q)
+    return Psi, V, Pt, Vt
+
+
+def power_spectrum_jvp(Psi, Pt, n, L, n_bins, order=2):
+    """Tangent of the binned P(k) of the CIC density of X = q + Psi along Psi':
+    P_b = (L^3/M^2) <|delta^|^2>_b, so P'_b = (L^3/M^2) <2 Re(conj(delta^) delta'^)>_b with
+    delta' = (M/N) scatter_dot_grad(Psi').  Returns (k_mean, P', counts)."""
+    N = Psi.shape[1]
+    npart = round(N ** (1.0 / 3.0))
+    X = np.mod(lattice(npart, L) + Psi, L)
+    delta = mesh.density_contrast(X, n, L, order)
+    dt = (n ** 3 / N) * mesh.scatter_dot_grad(X, Pt, n, L, order)
+    dk, dtk = np.fft.fftn(delta), np.fft.fftn(dt)
+    k1 = mesh.wavenumbers(n, L)
+    kz, ky, kx = np.meshgrid(k1, k1, k1, indexing="ij")
+    kmag = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    kF = 2 * math.pi / L
+    b = np.floor(kmag / kF - 0.5).astype(np.int64)
+    ok = (kmag > 0) & (b >= 0) & (b < n_bins)
+    cross = 2.0 * (np.conj(dk) * dtk).real
+    cnt = np.bincount(b[ok], minlength=n_bins)[:n_bins]
+    ksum = np.bincount(b[ok], weights=kmag[ok], minlength=n_bins)[:n_bins]
+    psum = np.bincount(b[ok], weights=cross[ok], minlength=n_bins)[:n_bins]
+    M = n ** 3
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return (np.where(cnt > 0, ksum / np.maximum(cnt, 1), 0.0),
+                np.where(cnt > 0, psum / np.maximum(cnt, 1) * L ** 3 / M ** 2, 0.0), cnt)
+
+
+# --------------------------------------------------------------------------
 # adjoint (Sec. 2.7, Table 5; App. C)
 # --------------------------------------------------------------------------
 

@@ -236,3 +236,73 @@ def test_interlaced_force_is_closer_to_newtonian():
             np.testing.assert_allclose(A[:, 0], -A[:, 1], atol=1e-10)
         res[inter] = np.std(vals) / abs(np.mean(vals))
     assert res[True] < res[False]
+
+
+# ---------------------------------------------------------------- forward mode (JVPs)
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_scatter_dot_grad_is_the_scatter_tangent(order):
+    # central differences of the (smooth-kernel) scatter along T, and the exact
+    # transpose identity <scatter_dot_grad(T), m> = sum_i T_i . gather_grad(m)_i
+    n, L = 8, 8.0
+    rng = np.random.default_rng(21)
+    X = rng.uniform(0, L, size=(3, 40))
+    T = rng.normal(size=(3, 40))
+    eps = 1e-6
+    fd = (mesh.scatter(X + eps * T, None, n, L, order) - mesh.scatter(X - eps * T, None, n, L, order)) / (2 * eps)
+    jv = mesh.scatter_dot_grad(X, T, n, L, order)
+    assert np.max(np.abs(jv - fd)) < 1e-7 * max(1.0, np.max(np.abs(fd)))
+    m = rng.normal(size=(n, n, n))
+    lhs = np.sum(jv * m)
+    rhs = np.sum(T * mesh.gather_grad(m, X, L, order))
+    assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-12)
+
+
+def test_accel_jvp_dot_product_with_vjp_and_finite_differences():
+    n, L = 16, 100.0
+    cfg = nbody.Config(n_part=n, n_mesh=n, box=L, order=3)
+    rng = np.random.default_rng(22)
+    q = nbody.lattice(n, L)
+    P = rng.normal(scale=2.0, size=(3, n ** 3))
+    T = rng.normal(size=(3, n ** 3))
+    u = rng.normal(size=(3, n ** 3))
+    Dh = 0.4
+    jt = nbody.accel_jvp(cfg, P, q, Dh, T)
+    vu = nbody.accel_vjp(cfg, P, q, Dh, u)
+    assert np.sum(u * jt) == pytest.approx(np.sum(vu * T), rel=1e-10)
+    eps = 1e-4
+    fd = (nbody.accel(cfg, P + eps * T, q, Dh) - nbody.accel(cfg, P - eps * T, q, Dh)) / (2 * eps)
+    assert np.max(np.abs(jt - fd)) < 1e-5 * np.max(np.abs(fd))
+
+
+def test_run_jvp_matches_finite_differences():
+    n, L = 16, 128.0
+    cfg = nbody.Config(n_part=n, n_mesh=n, box=L, order=3, n_steps=3)
+    w = np.random.default_rng(23).standard_normal((n, n, n))
+    wt = np.random.default_rng(24).standard_normal((n, n, n))
+    P0, V0 = nbody.zeldovich_ic(cfg, w)
+    Pt0, Vt0 = nbody.zeldovich_ic(cfg, wt)          # the ICs are linear in the noise
+    P, V, Pt, Vt = nbody.run_jvp(cfg, P0, V0, Pt0, Vt0)
+    eps = 1e-5
+    Pp, Vp = nbody.run(cfg, *nbody.zeldovich_ic(cfg, w + eps * wt))
+    Pm, Vm = nbody.run(cfg, *nbody.zeldovich_ic(cfg, w - eps * wt))
+    np.testing.assert_allclose(Pt, (Pp - Pm) / (2 * eps), atol=1e-6 * np.max(np.abs(Pt)))
+    np.testing.assert_allclose(Vt, (Vp - Vm) / (2 * eps), atol=1e-6 * np.max(np.abs(Vt)))
+    ref_P, _ = nbody.run(cfg, P0, V0)
+    np.testing.assert_allclose(P, ref_P, atol=1e-12)
+
+
+def test_power_spectrum_jvp_matches_finite_differences():
+    n, L = 16, 100.0
+    rng = np.random.default_rng(25)
+    P = rng.normal(scale=3.0, size=(3, n ** 3))
+    T = rng.normal(size=(3, n ** 3))
+    k, dpk, cnt = nbody.power_spectrum_jvp(P, T, n, L, 8, order=3)
+    eps = 1e-5
+    X = nbody.lattice(n, L)
+
+    def pk(Q):
+        return mesh.power_spectrum(mesh.density_contrast(np.mod(X + Q, L), n, L, 3), L, 8)[1]
+
+    fd = (pk(P + eps * T) - pk(P - eps * T)) / (2 * eps)
+    np.testing.assert_allclose(dpk, fd, rtol=1e-6, atol=1e-9 * np.max(np.abs(fd)))
