@@ -332,6 +332,45 @@ def scaleup_benchmark(dev, reps=3):
             "ms_per_pm_step": ms / 10, "particle_steps_per_s": n ** 3 * 10 / (ms / 1e3)}
 
 
+def jvp_benchmark(dev, reps=5):
+    """Forward mode on the adjoint workload (128^3 / 128^3, L = 500, 10 steps):
+    tangent ICs + the run with its tangent, and the P(k) tangent of the result."""
+    import numpy as np
+    import torch
+    from paper_2510_05206_gb300 import PM, Config
+    n = 128
+    pm = PM(Config(n_part=n, n_mesh=n, box=500.0, n_steps=10), device=dev)
+    rng = np.random.default_rng(NOISE_SEED + 5)
+    w = torch.from_numpy(rng.standard_normal((1, n ** 3), dtype=np.float32)).to(dev)
+    wt = torch.from_numpy(rng.standard_normal((1, n ** 3), dtype=np.float32)).to(dev)
+    d, v = pm.new_state()
+    td, tv = pm.new_state()
+
+    def once():
+        pm.ic_zeldovich(w, d, v)
+        pm.ic_zeldovich(wt, td, tv)
+        pm.jvp(d, v, td, tv)
+
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        once()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    tp = time.perf_counter()
+    for _ in range(reps):
+        pm.power_spectrum_jvp(d, td, n, n // 2)
+    ms_pk = (time.perf_counter() - tp) * 1e3 / reps
+    pm.close()
+    return {"workload": "jvp_128cubed_on_128cubed_L500_10step_cic", "ms_per_jvp_run": ms,
+            "particle_steps_per_s_with_tangent": n ** 3 * 10 / (ms / 1e3), "ms_per_pk_jvp_host_timed": ms_pk}
+
+
 def lpt2_ic_benchmark(dev, reps=3):
     """2LPT initial conditions for the 512^3 lattice (four spectral chains and
     the source products) against the Zel'dovich ICs of the same handle size."""
@@ -529,6 +568,7 @@ def main():
         line["scaleup"] = scaleup_benchmark(dev)
         line["deconvolve"] = deconvolve_benchmark(dev)
         line["lpt2_ic"] = lpt2_ic_benchmark(dev)
+        line["jvp"] = jvp_benchmark(dev)
     if not args.no_serving:
         line["serving"] = serving_benchmark(args.serve_requests, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

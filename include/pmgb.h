@@ -157,6 +157,13 @@ int pm_step_slots(pm_handle* h, float* disp, float* vel);
 int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n_mesh, int32_t n_bins, double* k, double* pk,
                       int64_t* n_modes);
 
+/* Forward mode of pm_power_spectrum: with the tangent tdisp of disp, dpk[slot][bin]
+ * = (L^3/M^2) <2 Re(conj(delta^) delta'^)> over the bin's modes (delta' the CIC
+ * density tangent of X = q + disp along tdisp, times M/N); k, pk, n_modes as
+ * pm_power_spectrum (which it also runs).  Synchronises the stream. */
+int pm_power_spectrum_jvp(pm_handle* h, const float* disp, const float* tdisp, int32_t n_mesh, int32_t n_bins,
+                          double* k, double* pk, double* dpk, int64_t* n_modes);
+
 /* Density contrast delta = rho M / N - 1 of X = q + disp on an n_mesh^3 mesh with
  * kernel `order` (Table 1), every slot: delta [slot][n_mesh^3] device. */
 int pm_density(pm_handle* h, const float* disp, int32_t n_mesh, int32_t order, float* delta);
@@ -181,6 +188,19 @@ int pm_interp(pm_handle* h, const float* disp, const float* force, float* acc);
  * Single grid only (interlace = 0, else PM_ERR_UNSUPPORTED).  Allocates three
  * adjoint meshes per slot on its first call. */
 int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adj_disp, float* adj_vel, int32_t step_end);
+
+/* Forward mode (Jacobian-vector products; the tangent counterpart of App. C's
+ * scatter/gather derivatives): advances the state (disp, vel) and a tangent
+ * (tdisp, tvel), same layout, through steps [step_begin, step_end) of the DKD
+ * stepper.  Per step: X_half and X'_half = X' + tau1 V'; the density of X_half
+ * and its tangent rho'_j = sum_i X'_half,i . grad_X W(r_j - X_i); the force
+ * operator applied to both (it is linear); A = gather(g) and
+ * A' = gather(g') + X'_half . grad gather(g); V' <- alpha V' + kick A', X' <- X'_half
+ * + tau2 V'.  Tangent ICs come from pm_ic_zeldovich on the tangent noise (the ICs
+ * are linear in the noise).  Single grid only (interlace = 0, else
+ * PM_ERR_UNSUPPORTED).  Allocates a tangent density and force mesh per slot on
+ * its first call. */
+int pm_jvp(pm_handle* h, float* disp, float* vel, float* tdisp, float* tvel, int32_t step_begin, int32_t step_end);
 
 /* Pullback through the Zel'dovich initial conditions: with psi1* = D(a_ini)
  * adj_disp + adj_vel, adj_noise = sum_c F_c^T psi1*_c (F_c: noise -> psi1_c);

@@ -217,7 +217,7 @@ struct ZArgs {
 };
 
 enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5, Z_POT = 6, Z_POT_IL = 7,
-       Z_IC_D2 = 8, Z_IC_O2 = 9, Z_LPT2 = 10, Z_DEC = 16 };
+       Z_IC_D2 = 8, Z_IC_O2 = 9, Z_LPT2 = 10, Z_PKX = 11, Z_DEC = 16 };
 
 // MODE_DEC = mode | Z_DEC: the mode's multiplier also divides by the squared mass
 // assignment kernel (deconvolution tables in a.dec1), compiled only where used.
@@ -283,13 +283,15 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
     }
 
     fft_io<n, COL_TILE, -1, false, true>(in0, A, A, tw, 1);
-    if (MODE == Z_FORCE_IL || MODE == Z_POT_IL) {
+    if (MODE == Z_FORCE_IL || MODE == Z_POT_IL || MODE == Z_PKX) {
         __syncthreads();
         fft_io<n, COL_TILE, -1, false, true>(GCols{const_cast<float2*>(a.in[1]) + off, ES}, A2, A2, tw, 1);
     }
     __syncthreads();
 
-    if (MODE == Z_PK) {
+    if (MODE == Z_PK || MODE == Z_PKX) {
+        // Z_PKX (forward mode of P(k)): the same sums of w 2 Re(conj(delta^) delta'^)
+        // with delta'^ the transform of in[1] (in A2).
         // sum over the modes of each bin of w |delta^|^2 (w = 2 for 0 < kx < n/2, the
         // half spectrum standing for +-kx), FP64 per bin: runs of equal bin along kz
         // are summed per thread, then added to a per-warp (or shared) FP64 accumulator
@@ -320,12 +322,13 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
                 const int e = e0 + k, mz = freq_index(e, n);
                 const int bk = __ldg(&a.bintab[kxy + mz * mz]);
                 const float2 d = A(l, e);
+                const float2 dt = MODE == Z_PKX ? A2(l, e) : d;
                 if (bk != cur) {
                     if (cur >= 0) atomicAdd(&wacc[cur], (double)run);
                     cur = bk;
                     run = 0.f;
                 }
-                run += wx * (d.x * d.x + d.y * d.y);
+                run += (MODE == Z_PKX ? 2.f * wx : wx) * (d.x * dt.x + d.y * dt.y);
             }
             if (cur >= 0) atomicAdd(&wacc[cur], (double)run);
         }
@@ -506,7 +509,7 @@ template <int LOG2N, int MODE>
 void launch_z_mode(const ZArgs& a, int nslots, cudaStream_t st) {
     constexpr int n = 1 << LOG2N;
     constexpr int M = MODE & (Z_DEC - 1);
-    const int ntile = (M == Z_FORCE_IL || M == Z_ADJ || M == Z_IC_ADJ || M == Z_POT_IL) ? 3 : 2;
+    const int ntile = (M == Z_FORCE_IL || M == Z_ADJ || M == Z_IC_ADJ || M == Z_POT_IL || M == Z_PKX) ? 3 : 2;
     const size_t smem = (size_t)(ntile * col_tile_elems(n) + 2 * n + ((MODE & Z_DEC) ? n / 2 : 0)) * sizeof(float2);
     dim3 grid(n / 2 / COL_TILE + 1, n, nslots);
     set_smem(k_fft_z<LOG2N, MODE>, smem);
@@ -530,6 +533,7 @@ void launch_z(int mode, const ZArgs& a, int nslots, cudaStream_t st) {
         case Z_IC_O2: launch_z_mode<LOG2N, Z_IC_O2>(a, nslots, st); break;
         case Z_LPT2: launch_z_mode<LOG2N, Z_LPT2>(a, nslots, st); break;
         case Z_PK: launch_z_mode<LOG2N, Z_PK>(a, nslots, st); break;
+        case Z_PKX: launch_z_mode<LOG2N, Z_PKX>(a, nslots, st); break;
         case Z_ADJ:
             if (dec) launch_z_mode<LOG2N, Z_ADJ | Z_DEC>(a, nslots, st);
             else launch_z_mode<LOG2N, Z_ADJ>(a, nslots, st);

@@ -1039,6 +1039,133 @@ __global__ void __launch_bounds__(256) k_adj_gather_grad(PmGeom g, float* __rest
     }
 }
 
+// ------------------------------------------------------------------ forward mode
+// Tangents of the DKD step (the JVP counterpart of App. C): the deposit
+// pushes forward as rho'_j = sum_i sum_d X'_di dW(r_j - X_i)/dX_di, the force
+// operator is linear (g' = G rho'), and the gather as
+// A'_c = gather(g'_c) + sum_d X'_d d/dX_d gather(g_c).
+
+// DRIFT = 1: X_half = X + tau1 V, X'_half = X' + tau1 V' (written back); then the
+// deposit of X_half into rho and of its tangent into trho.  DRIFT = 0: no drift
+// and nothing written back (P(k) tangents).
+template <int ORDER, int DRIFT>
+__global__ void __launch_bounds__(256) k_jvp_drift_deposit(PmGeom g, float* __restrict__ disp,
+                                                           const float* __restrict__ vel, float* __restrict__ tdisp,
+                                                           const float* __restrict__ tvel,
+                                                           const SlotCoef* __restrict__ coef, int cstride,
+                                                           float* __restrict__ rho, float* __restrict__ trho) {
+    const int slot = blockIdx.y;
+    const SlotCoef cf = coef[slot * cstride];
+    if (!cf.active) return;
+    const long long N = 1ll << (3 * g.log2np);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const Lattice L = lattice_index(i, g.log2np);
+    const long long o = slot * g.slot_part;
+    float p[3], t[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        p[c] = disp[o + c * N + i];
+        t[c] = tdisp[o + c * N + i];
+        if (DRIFT) {
+            p[c] += cf.tau1 * vel[o + c * N + i];
+            t[c] += cf.tau1 * tvel[o + c * N + i];
+            disp[o + c * N + i] = p[c];
+            tdisp[o + c * N + i] = t[c];
+        }
+        t[c] *= g.inv_h;                            // d/dX = inv_h d/du
+    }
+    const int ds = g.log2ng - g.log2np;
+    const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[0] * g.inv_h);
+    const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[1] * g.inv_h);
+    const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[2] * g.inv_h);
+    const int ng = 1 << g.log2ng, msk = ng - 1;
+    float* m = rho ? rho + slot * g.slot_mesh : nullptr;
+    float* tm = trho + slot * g.slot_mesh;
+#pragma unroll
+    for (int c = 0; c < ORDER; ++c) {
+        const long long zo = (long long)((az.c + c) & msk) * ng;
+#pragma unroll
+        for (int b = 0; b < ORDER; ++b) {
+            const long long yo = (zo + ((ay.c + b) & msk)) * ng;
+#pragma unroll
+            for (int a = 0; a < ORDER; ++a) {
+                const long long j = yo + ((ax.c + a) & msk);
+                if (m) atomicAdd(&m[j], az.w[c] * ay.w[b] * ax.w[a]);
+                const float dv = t[0] * ax.dw[a] * ay.w[b] * az.w[c] + t[1] * ax.w[a] * ay.dw[b] * az.w[c] +
+                                 t[2] * ax.w[a] * ay.w[b] * az.dw[c];
+                atomicAdd(&tm[j], dv);
+            }
+        }
+    }
+}
+
+// At X_half: A = gather(g), A' = gather(g') + X'_half . grad gather(g); then the
+// kick and drift_2 of the state and of its tangent.
+template <int ORDER>
+__global__ void __launch_bounds__(256) k_jvp_interp_kick(PmGeom g, float* __restrict__ disp, float* __restrict__ vel,
+                                                         float* __restrict__ tdisp, float* __restrict__ tvel,
+                                                         const SlotCoef* __restrict__ coef, int cstride,
+                                                         const float4* __restrict__ force4,
+                                                         const float4* __restrict__ tforce4) {
+    const int slot = blockIdx.y;
+    const SlotCoef cf = coef[slot * cstride];
+    if (!cf.active) return;
+    const long long N = 1ll << (3 * g.log2np);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const Lattice L = lattice_index(i, g.log2np);
+    const long long o = slot * g.slot_part;
+    float p[3], t[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        p[c] = disp[o + c * N + i];
+        t[c] = tdisp[o + c * N + i];
+    }
+    const int ds = g.log2ng - g.log2np;
+    const AxisTaps ax = axis_taps<ORDER>(L.ix, ds, p[0] * g.inv_h);
+    const AxisTaps ay = axis_taps<ORDER>(L.iy, ds, p[1] * g.inv_h);
+    const AxisTaps az = axis_taps<ORDER>(L.iz, ds, p[2] * g.inv_h);
+    const int ng = 1 << g.log2ng, msk = ng - 1;
+    const long long M = 1ll << (3 * g.log2ng);
+    const float4* f = force4 + slot * M;
+    const float4* tf = tforce4 + slot * M;
+    float A[3] = {0.f, 0.f, 0.f}, At[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < ORDER; ++c) {
+        const long long zo = (long long)((az.c + c) & msk) * ng;
+#pragma unroll
+        for (int b = 0; b < ORDER; ++b) {
+            const long long yo = (zo + ((ay.c + b) & msk)) * ng;
+#pragma unroll
+            for (int a = 0; a < ORDER; ++a) {
+                const long long j = yo + ((ax.c + a) & msk);
+                const float w = az.w[c] * ay.w[b] * ax.w[a];
+                // X'_half . grad of the tap weight (per unit length)
+                const float dw = g.inv_h * (t[0] * ax.dw[a] * ay.w[b] * az.w[c] + t[1] * ax.w[a] * ay.dw[b] * az.w[c] +
+                                            t[2] * ax.w[a] * ay.w[b] * az.dw[c]);
+                const float4 gv = __ldg(&f[j]);
+                const float4 tv = __ldg(&tf[j]);
+                A[0] += w * gv.x;
+                A[1] += w * gv.y;
+                A[2] += w * gv.z;
+                At[0] += w * tv.x + dw * gv.x;
+                At[1] += w * tv.y + dw * gv.y;
+                At[2] += w * tv.z + dw * gv.z;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float v = cf.alpha * vel[o + c * N + i] + cf.kick * A[c];
+        const float vt = cf.alpha * tvel[o + c * N + i] + cf.kick * At[c];
+        vel[o + c * N + i] = v;
+        tvel[o + c * N + i] = vt;
+        disp[o + c * N + i] = p[c] + cf.tau2 * v;
+        tdisp[o + c * N + i] = t[c] + cf.tau2 * vt;
+    }
+}
+
 // per-slot FP64 dot products sum_i a_i b_i over n floats (slot stride n)
 __global__ void __launch_bounds__(256) k_dot(const float* __restrict__ a, const float* __restrict__ b, long long n,
                                             double* __restrict__ out) {
@@ -1248,5 +1375,31 @@ int pm_div_stencil(int grad_order, int log2n, float inv_h, const float* s3, long
 int pm_lpt2_source(int pass, const float* t, float* mu, long long n, int nslots, cudaStream_t st) {
     dim3 grid((unsigned)((n + 255) / 256), nslots);
     k_lpt2_source<<<grid, 256, 0, st>>>(pass, t, mu, n);
+    return 0;
+}
+
+int pm_jvp_drift_deposit(int order, int drift, const PmGeom& g, float* disp, const float* vel, float* tdisp,
+                         const float* tvel, const SlotCoef* coef, int cstride, float* rho, float* trho, int nslots,
+                         cudaStream_t st) {
+    const long long N = 1ll << (3 * g.log2np);
+    dim3 grid((unsigned)((N + 255) / 256), nslots);
+#define PM_JD(O, D) k_jvp_drift_deposit<O, D><<<grid, 256, 0, st>>>(g, disp, vel, tdisp, tvel, coef, cstride, rho, trho)
+    if (order == 2) { if (drift) PM_JD(2, 1); else PM_JD(2, 0); }
+    else if (order == 3) { if (drift) PM_JD(3, 1); else PM_JD(3, 0); }
+    else if (order == 4) { if (drift) PM_JD(4, 1); else PM_JD(4, 0); }
+    else return -1;
+#undef PM_JD
+    return 0;
+}
+
+int pm_jvp_interp_kick(int order, const PmGeom& g, float* disp, float* vel, float* tdisp, float* tvel,
+                       const SlotCoef* coef, int cstride, const float4* force4, const float4* tforce4, int nslots,
+                       cudaStream_t st) {
+    const long long N = 1ll << (3 * g.log2np);
+    dim3 grid((unsigned)((N + 255) / 256), nslots);
+    if (order == 2) k_jvp_interp_kick<2><<<grid, 256, 0, st>>>(g, disp, vel, tdisp, tvel, coef, cstride, force4, tforce4);
+    else if (order == 3) k_jvp_interp_kick<3><<<grid, 256, 0, st>>>(g, disp, vel, tdisp, tvel, coef, cstride, force4, tforce4);
+    else if (order == 4) k_jvp_interp_kick<4><<<grid, 256, 0, st>>>(g, disp, vel, tdisp, tvel, coef, cstride, force4, tforce4);
+    else return -1;
     return 0;
 }

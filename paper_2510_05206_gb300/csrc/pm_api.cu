@@ -71,6 +71,8 @@ struct pm_handle {
     std::map<int, std::vector<pmcosmo::StepCoef>> tables_by_nsteps;
     // adjoint scratch: 3 meshes per slot of max(Mg, Np) floats (allocated on first use)
     float* adj3 = nullptr;
+    float* jrho = nullptr;       // forward mode: tangent density [B][rho_slot]
+    float4* jforce = nullptr;    // forward mode: tangent force mesh [B][Mg]
     double* d_dot = nullptr;
     // host-buffer mode
     float *d_noise = nullptr, *d_disp = nullptr, *d_vel = nullptr;
@@ -614,6 +616,8 @@ void pm_destroy(pm_handle* h) {
     cudaFree(h->d_pk);
     for (auto& kv : h->bintabs) cudaFree(kv.second.d_tab);
     cudaFree(h->adj3);
+    cudaFree(h->jrho);
+    cudaFree(h->jforce);
     cudaFree(h->d_dot);
     cudaFree(h->d_noise);
     cudaFree(h->d_disp);
@@ -817,6 +821,59 @@ int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n, int32_t nbins,
     return PM_OK;
 }
 
+namespace {
+int jvp_alloc(pm_handle* h);   // tangent density and force mesh, allocated on first use
+}
+
+int pm_power_spectrum_jvp(pm_handle* h, const float* disp, const float* tdisp, int32_t n, int32_t nbins, double* k,
+                          double* pk, double* dpk, int64_t* nmodes) {
+    if (!h) return PM_ERR_ARG;
+    if (!tdisp || !dpk) return h->fail(PM_ERR_ARG, "pm_power_spectrum_jvp: NULL buffer");
+    // P(k) itself (allocates and validates as pm_power_spectrum)
+    int rc = pm_power_spectrum(h, disp, n, nbins, k, pk, nmodes);
+    if (rc) return rc;
+    if ((rc = jvp_alloc(h))) return rc;
+    const pm_handle::BinTable* bt = nullptr;
+    if ((rc = bintab_for(h, n, nbins, &bt))) return rc;
+    cudaStream_t st = h->stream;
+    const int l2 = ilog2i(n);
+    const long long S = spec_elems(n);
+    // the CIC density of X and its tangent along X' on the n-mesh; then the binned
+    // cross spectrum 2 Re(conj(delta^) delta'^) (rho tangent in the second spectrum)
+    cudaMemsetAsync(h->rho, 0, sizeof(float) * h->rho_slot() * h->B, st);
+    cudaMemsetAsync(h->jrho, 0, sizeof(float) * h->rho_slot() * h->B, st);
+    cudaMemsetAsync(h->d_pk, 0, sizeof(double) * h->B * nbins, st);
+    pm_jvp_drift_deposit(2, 0, geom(h, n, h->rho_slot()), const_cast<float*>(disp), nullptr,
+                         const_cast<float*>(tdisp), nullptr, h->d_unit, 0, h->rho, h->jrho, h->B, st);
+    pm_fft_r2c_x(l2, h->rho, h->rho_slot(), h->spec, h->spec_slot(), h->B, h->d_tw[l2], st);
+    pm_fft_r2c_x(l2, h->jrho, h->rho_slot(), h->spec + S, h->spec_slot(), h->B, h->d_tw[l2], st);
+    pm_fft_y(l2, h->spec, h->spec_slot(), h->B, -1, h->d_tw[l2], st);
+    pm_fft_y(l2, h->spec + S, h->spec_slot(), h->B, -1, h->d_tw[l2], st);
+    PmZPass z{};
+    z.in[0] = h->spec;
+    z.in[1] = h->spec + S;
+    z.slot_stride = h->spec_slot();
+    z.tw = h->d_tw[l2];
+    z.bintab = bt->d_tab;
+    z.pk_out = h->d_pk;
+    z.nbins = nbins;
+    pm_fft_z(l2, PM_Z_PKX, z, h->B, st);
+    if ((rc = h->check_launch("power spectrum jvp"))) return rc;
+    std::vector<double> acc((size_t)h->B * nbins);
+    if (cudaMemcpyAsync(acc.data(), h->d_pk, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return h->fail(PM_ERR_CUDA, "power spectrum jvp readback: %s", cudaGetErrorString(cudaGetLastError()));
+    const long long M = mesh_elems(n);
+    const double L = h->cfg.box, MN = (double)M / (double)h->Np();
+    for (int b = 0; b < h->B; ++b)
+        for (int i = 0; i < nbins; ++i) {
+            const double cnt = bt->count[i];
+            const size_t o = (size_t)b * nbins + i;
+            dpk[o] = cnt > 0 ? acc[o] / cnt * MN * MN * L * L * L / ((double)M * (double)M) : 0.0;
+        }
+    return PM_OK;
+}
+
 int pm_density(pm_handle* h, const float* disp, int32_t n, int32_t order, float* delta) {
     if (!h) return PM_ERR_ARG;
     if (!disp || !delta) return h->fail(PM_ERR_ARG, "pm_density: NULL buffer");
@@ -847,6 +904,13 @@ int pm_interp(pm_handle* h, const float* disp, const float* force, float* acc) {
 }
 
 namespace {
+int jvp_alloc(pm_handle* h) {
+    if (h->jrho) return PM_OK;
+    int rc = dalloc(h, &h->jrho, (size_t)h->B * h->rho_slot(), "tangent density");
+    if (rc) return rc;
+    return dalloc(h, &h->jforce, (size_t)h->B * h->Mg(), "tangent force mesh");
+}
+
 int adj_alloc(pm_handle* h) {
     if (h->adj3) return PM_OK;
     int rc = dalloc(h, &h->adj3, (size_t)h->B * 3 * std::max(h->Mg(), h->Np()), "adjoint meshes");
@@ -854,6 +918,37 @@ int adj_alloc(pm_handle* h) {
     return dalloc(h, &h->d_dot, (size_t)h->B, "adjoint dot");
 }
 }  // namespace
+
+int pm_jvp(pm_handle* h, float* disp, float* vel, float* tdisp, float* tvel, int32_t b, int32_t e) {
+    if (!h) return PM_ERR_ARG;
+    if (!disp || !vel || !tdisp || !tvel) return h->fail(PM_ERR_ARG, "pm_jvp: NULL buffer");
+    if (h->ngrids != 1) return h->fail(PM_ERR_UNSUPPORTED, "pm_jvp: interlaced grids are not supported");
+    if (b < 0 || e < b || e > (int)h->table.size())
+        return h->fail(PM_ERR_ARG, "pm_jvp: bad step range [%d, %d)", b, e);
+    int rc;
+    if ((rc = jvp_alloc(h))) return rc;
+    cudaStream_t st = h->stream;
+    const int n = h->ng, order = h->cfg.order;
+    const long long Mg = h->Mg();
+    const PmGeom gd = geom(h, n, h->rho_slot());
+    const PmGeom gf = geom(h, n, Mg);
+    const float scale = (float)(1.0 / (double)h->Np());
+    for (int s = b; s < e; ++s) {
+        const SlotCoef* coef = h->d_table + s;
+        cudaMemsetAsync(h->rho, 0, sizeof(float) * h->rho_slot() * h->B, st);
+        cudaMemsetAsync(h->jrho, 0, sizeof(float) * h->rho_slot() * h->B, st);
+        h->phase(0, 1);
+        pm_jvp_drift_deposit(order, 1, gd, disp, vel, tdisp, tvel, coef, 0, h->rho, h->jrho, h->B, st);
+        h->phase_end();
+        if ((rc = spectral_force(h, h->rho, h->rho_slot(), Mg, scale, nullptr, h->force, h->B))) return rc;
+        if ((rc = spectral_force(h, h->jrho, h->rho_slot(), Mg, scale, nullptr, h->jforce, h->B))) return rc;
+        h->phase(6, 1);
+        pm_jvp_interp_kick(order, gf, disp, vel, tdisp, tvel, coef, 0, h->force, h->jforce, h->B, st);
+        h->phase_end();
+        if ((rc = h->check_launch("pm_jvp step"))) return rc;
+    }
+    return PM_OK;
+}
 
 int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adisp, float* avel, int32_t step_end) {
     if (!h) return PM_ERR_ARG;

@@ -22,7 +22,7 @@ struct PmZPass {
 };
 
 enum { PM_Z_FORCE = 0, PM_Z_FORCE_IL = 1, PM_Z_IC = 2, PM_Z_PK = 3, PM_Z_ADJ = 4, PM_Z_IC_ADJ = 5, PM_Z_POT = 6,
-       PM_Z_POT_IL = 7, PM_Z_IC_D2 = 8, PM_Z_IC_O2 = 9, PM_Z_LPT2 = 10 };
+       PM_Z_POT_IL = 7, PM_Z_IC_D2 = 8, PM_Z_IC_O2 = 9, PM_Z_LPT2 = 10, PM_Z_PKX = 11 };
 
 // clear_in != 0: the input rows are zeroed after they are read (a density mesh
 // consumed here is then ready for the next deposit without a separate memset)
@@ -87,3 +87,15 @@ int pm_axpby(float* out, const float* x, const float* y, float a, float b, long 
 // pass 0 (diagonal psi_x,x, psi_y,y, psi_z,z): mu = t0 t1 + t0 t2 + t1 t2;
 // pass 1 (off-diagonal psi_x,y, psi_x,z, psi_y,z): mu = -(3/7) (mu - t0^2 - t1^2 - t2^2) = L^(2).
 int pm_lpt2_source(int pass, const float* t, float* mu, long long n, int nslots, cudaStream_t st);
+
+// Forward mode (tangents of the DKD step).  drift = 1: X_half = X + tau1 V and its
+// tangent (written back), then deposit X_half into rho (skipped when NULL) and
+// rho' = sum X'_half . grad W into trho; drift = 0: deposit of X and X' as given.
+int pm_jvp_drift_deposit(int order, int drift, const PmGeom& g, float* disp, const float* vel, float* tdisp,
+                         const float* tvel, const SlotCoef* coef, int cstride, float* rho, float* trho, int nslots,
+                         cudaStream_t st);
+// A = gather(g), A' = gather(g') + X' . grad gather(g) at X = disp (= X_half); kick and
+// drift_2 of the state and the tangent.
+int pm_jvp_interp_kick(int order, const PmGeom& g, float* disp, float* vel, float* tdisp, float* tvel,
+                       const SlotCoef* coef, int cstride, const float4* force4, const float4* tforce4, int nslots,
+                       cudaStream_t st);

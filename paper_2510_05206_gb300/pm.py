@@ -194,6 +194,27 @@ class PM:
         end = self.cfg.n_steps if step_end is None else step_end
         self._check(self.lib.pm_adjoint(self.h, _ptr(disp), _ptr(vel), _ptr(adj_disp), _ptr(adj_vel), int(end)))
 
+    def jvp(self, disp, vel, tdisp, tvel, begin=0, end=None):
+        """Forward mode in place: advances (disp, vel) and the tangent (tdisp, tvel)
+        through steps [begin, end) (default: all)."""
+        for t, nm in ((disp, "disp"), (vel, "vel"), (tdisp, "tdisp"), (tvel, "tvel")):
+            self._state_ok(t, nm, (self.B, 3, self.N))
+        self._stream()
+        end = self.cfg.n_steps if end is None else end
+        self._check(self.lib.pm_jvp(self.h, _ptr(disp), _ptr(vel), _ptr(tdisp), _ptr(tvel), int(begin), int(end)))
+
+    def power_spectrum_jvp(self, disp, tdisp, n_mesh=None, n_bins=None):
+        """(k, P, dP, counts): P(k) of disp and its tangent along tdisp."""
+        n = n_mesh or (self.cfg.pk_mesh_max or self.cfg.n_mesh)
+        nb = n_bins or n // 2
+        k, pk, dpk = np.zeros((self.B, nb)), np.zeros((self.B, nb)), np.zeros((self.B, nb))
+        cnt = np.zeros((self.B, nb), dtype=np.int64)
+        self._stream()
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._check(self.lib.pm_power_spectrum_jvp(self.h, _ptr(disp), _ptr(tdisp), int(n), int(nb), dptr(k), dptr(pk),
+                                                   dptr(dpk), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return k, pk, dpk, cnt
+
     def ic_adjoint(self, noise, adj_disp, adj_vel, with_sigma8=True):
         out = torch.empty((self.B, self.N), device=self.device, dtype=torch.float32)
         ds8 = np.zeros(self.B)
