@@ -18,8 +18,9 @@ It restates, step by step and in double precision, what the paper
   with optional deconvolution by the squared kernel (Sec. 2.5, Table 1),
   interlacing, and the binned power spectrum.
 * ``nbody``      - Zel'dovich and 2LPT initial conditions (Sec. 2.2, Eqs. LPT,
-  helmholtz, LPT_L_and_T), the DKD stepper (Eq. dkd), full runs, and the
-  adjoint method (Sec. 2.7, Table 5, App. C).
+  helmholtz, LPT_L_and_T), the DKD stepper (Eq. dkd), full runs, the
+  adjoint method (Sec. 2.7, Table 5, App. C) and its forward-mode counterpart
+  (tangents of the run and of P(k)).
 
 Readings of places where the paper is silent, ambiguous or garbled are stated
 in the docstring of the function that takes them.
