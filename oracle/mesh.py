@@ -154,6 +154,75 @@ def scatter_dot_grad(X, T, n, L, order, shift=0.0):
     return rho.reshape(n, n, n)
 
 
+# --------------------------------------------------------------------------
+# NUFFT force (Sec. 2.5, force evaluation with the non-uniform FFT)
+# --------------------------------------------------------------------------
+
+ES_WIDTH = 5                    # kernel support in fine-grid cells (5^3 taps)
+ES_BETA = 2.30 * ES_WIDTH       # shape parameter for a grid upsampled twice
+
+
+def es_kernel(t):
+    """Exponential-of-semicircle kernel exp(beta (sqrt(1 - z^2) - 1)), z = 2 t / w,
+    zero for |z| > 1 (t in fine-grid cells)."""
+    z = 2.0 * np.asarray(t, dtype=np.float64) / ES_WIDTH
+    return np.where(np.abs(z) <= 1.0, np.exp(ES_BETA * (np.sqrt(np.maximum(1.0 - z * z, 0.0)) - 1.0)), 0.0)
+
+
+def es_taps(u):
+    """The ES kernel's 5 cells around u (cells): nearest node i0 = floor(u + 1/2)
+    and its neighbours at -2..2, with their weights."""
+    i0 = np.floor(np.asarray(u) + 0.5).astype(np.int64)
+    return [(i0 + o, es_kernel(i0 + o - u)) for o in range(-2, 3)]
+
+
+def es_fourier(nf):
+    """Continuous transform of the ES kernel at the DFT frequencies of an nf-cell
+    axis, int phi(t) cos(kappa t) dt with kappa = 2 pi m / nf (adaptive quadrature)."""
+    from scipy import integrate
+    mf = np.fft.fftfreq(nf, 1.0 / nf)
+    half = ES_WIDTH / 2.0
+    return np.array([integrate.quad(lambda t: float(es_kernel(t)) * math.cos(2 * math.pi * m / nf * t),
+                                    -half, half, limit=400, epsabs=1e-14, epsrel=1e-12)[0] for m in mf])
+
+
+def nufft_force(X, n, L):
+    """Force at the particles by the NUFFT (type 1 then type 2) on a grid upsampled
+    twice, nf = 2 n: spread unit masses with the ES kernel, FFT, keep the modes with
+    |m_c| < n/2 on every axis, multiply by the exact m_c = -i k_c / (-k^2) and by
+    1/psi^(k)^2 (psi^ = prod of es_fourier: once for the spreading, once for the
+    interpolation back), inverse FFT with scale 1/N, interpolate with the ES kernel.
+    Approximates nufft_band_force to the kernel's accuracy.  X: (3, N)."""
+    N = X.shape[1]
+    nf = 2 * n
+    H = L / nf
+    t3 = [es_taps(X[c] / H) for c in range(3)]
+    rho = np.zeros((nf, nf, nf))
+    for iz, wz in t3[2]:
+        for iy, wy in t3[1]:
+            for ix, wx in t3[0]:
+                np.add.at(rho, (iz % nf, iy % nf, ix % nf), wz * wy * wx)
+    mf = np.fft.fftfreq(nf, 1.0 / nf)
+    dec = np.where(np.abs(mf) < n / 2, 1.0 / es_fourier(nf) ** 2, 0.0)
+    k1 = 2.0 * math.pi / L * mf
+    kz, ky, kx = np.meshgrid(k1, k1, k1, indexing="ij")
+    k2 = kx ** 2 + ky ** 2 + kz ** 2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = np.where(k2 > 0, 1.0 / k2, 0.0)
+    D = dec[:, None, None] * dec[None, :, None] * dec[None, None, :]
+    rk = np.fft.fftn(rho)
+    out = np.zeros((3, N))
+    for c, kc in enumerate((kx, ky, kz)):
+        g = np.fft.ifftn(1j * kc * inv * D * rk).real * nf ** 3 / N
+        acc = np.zeros(N)
+        for iz, wz in t3[2]:
+            for iy, wy in t3[1]:
+                for ix, wx in t3[0]:
+                    acc += wz * wy * wx * g[iz % nf, iy % nf, ix % nf]
+        out[c] = acc
+    return out
+
+
 def density_contrast(X, n, L, order, shift=0.0):
     """delta_j = rho_j M / N - 1 with unit particle masses (Sec. 2.5, Fourier density with PM)."""
     N = X.shape[1]

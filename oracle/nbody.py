@@ -36,6 +36,7 @@ class Config:
     zero_corner: bool = True
     deconvolve: bool = False    # divide the force's density by the squared kernel (Table 4 `deconvolve`)
     lpt_order: int = 1          # 1 = Zel'dovich ICs, 2 = 2LPT ICs (Table 4 `nlpt_order_ics`)
+    nufft: bool = False         # force by the NUFFT on the n_mesh band (Sec. 2.5; ES kernel, grid 2 n_mesh)
     growth: object = field(default=None, repr=False)
 
     @property
@@ -137,6 +138,36 @@ def zeldovich_ic(cfg, w, pk=None):
 # force at the particles (Sec. 2.5)
 # --------------------------------------------------------------------------
 
+def nufft_band_force(X, n, L):
+    """Force at the particles from the non-uniform DFT of their positions,
+    restricted to the band of an n^3 mesh (Sec. 2.5, force evaluation with the
+    non-uniform FFT): delta^(k) = (M/N) sum_i exp(-i k.X_i) for the modes with
+    |m_c| < n/2 on every axis (k != 0; M = n^3), g_c^ = m_c delta^ with the exact
+    multiplier m_c = -i k_c / (-k^2), and g_c(X_i) = (1/M) sum_k g_c^(k) exp(i k.X_i)
+    evaluated exactly at each particle.  This is the plain definition that a
+    NUFFT approximates to its kernel's accuracy.  X: (3, N); returns (3, N)."""
+    N = X.shape[1]
+    M = n ** 3
+    m1 = np.arange(-(n // 2) + 1, n // 2)
+    mz, my, mx = np.meshgrid(m1, m1, m1, indexing="ij")
+    kv = 2.0 * math.pi / L * np.stack([mx.reshape(-1), my.reshape(-1), mz.reshape(-1)])   # (3, K)
+    k2 = (kv ** 2).sum(axis=0)
+    keep = k2 > 0
+    kv, k2 = kv[:, keep], k2[keep]
+    dk = np.zeros(kv.shape[1], dtype=complex)
+    for c0 in range(0, N, 2048):
+        ph = kv.T @ X[:, c0:c0 + 2048]                  # (K, chunk)
+        dk += np.exp(-1j * ph).sum(axis=1)
+    dk *= M / N
+    out = np.zeros((3, N))
+    for c in range(3):
+        gk = (1j * kv[c] / k2) * dk                     # -(i k_c) / (-k^2) delta^
+        for c0 in range(0, N, 2048):
+            ph = kv.T @ X[:, c0:c0 + 2048]
+            out[c, c0:c0 + 2048] = (gk[:, None] * np.exp(1j * ph)).sum(axis=0).real / M
+    return out
+
+
 def accel(cfg, Psi, q, Dh):
     """A(X) = g(X) / D_half^2 with g = -grad Lap^-1 delta (units of length).
 
@@ -153,6 +184,8 @@ def accel(cfg, Psi, q, Dh):
     """
     n, L = cfg.n_mesh, cfg.box
     X = np.mod(q + Psi, L)
+    if cfg.nufft:
+        return mesh.nufft_force(X, n, L) / Dh ** 2
     if not cfg.interlace:
         delta = mesh.density_contrast(X, n, L, cfg.order)
         g = mesh.force_field(delta, L, cfg.grad_order, cfg.lap_order, cfg.deconv_order)

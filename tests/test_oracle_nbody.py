@@ -306,3 +306,56 @@ def test_power_spectrum_jvp_matches_finite_differences():
 
     fd = (pk(P + eps * T) - pk(P - eps * T)) / (2 * eps)
     np.testing.assert_allclose(dpk, fd, rtol=1e-6, atol=1e-9 * np.max(np.abs(fd)))
+
+
+# ---------------------------------------------------------------- NUFFT force (exact band DFT)
+
+def test_nufft_band_force_conserves_momentum_and_matches_pm_on_band_limited_density():
+    n, L = 8, 40.0
+    rng = np.random.default_rng(31)
+    X = rng.uniform(0, L, size=(3, 300))
+    A = nbody.nufft_band_force(X, n, L)
+    # odd imaginary multiplier and |delta^|^2 even: the total force vanishes
+    assert np.max(np.abs(A.sum(axis=1))) < 1e-10 * np.max(np.abs(A))
+    # particles on the lattice, displaced along x by a single band mode: delta is then
+    # band-limited to first order and the force equals the exact-kernel PM force at
+    # the lattice points to second order in the amplitude
+    n = 16
+    q = nbody.lattice(n, L)
+    eps, kk = 1e-4, 2 * math.pi * 3 / L
+    Psi = np.zeros_like(q)
+    Psi[0] = eps * np.sin(kk * q[0])
+    A = nbody.nufft_band_force(q + Psi, n, L)
+    # linear theory: delta = -div Psi = -eps k cos(k x), g = -grad Lap^-1 delta = +eps sin(k x)
+    # (x only): the force is the displacement, as Zel'dovich consistency requires
+    np.testing.assert_allclose(A[0], eps * np.sin(kk * q[0]), atol=1e-3 * eps)
+    assert np.max(np.abs(A[1:])) < 1e-3 * eps
+
+
+def test_es_nufft_approximates_the_band_dft():
+    # the NUFFT algorithm (ES kernel, width 5, beta = 2.3 w, grid upsampled twice,
+    # deconvolution by the kernel's continuous transform both ways) against the
+    # exact band DFT: error ~1e-4 of the force, the 10^-(w-1) accuracy expected of a
+    # width-5 ES kernel at upsampling 2
+    n, L = 8, 40.0
+    X = np.random.default_rng(32).uniform(0, L, size=(3, 400))
+    out = mesh.nufft_force(X, n, L)
+    ref = nbody.nufft_band_force(X, n, L)
+    assert np.max(np.abs(out - ref)) < 2e-4 * np.max(np.abs(ref))
+    # a denser, smoother (lattice + small displacement) distribution: closer still
+    n = 16
+    q = nbody.lattice(n, L)
+    X = np.mod(q + np.random.default_rng(33).normal(scale=0.5, size=q.shape), L)
+    out = mesh.nufft_force(X, n, L)
+    ref = nbody.nufft_band_force(X, n, L)
+    assert np.max(np.abs(out - ref)) < 2e-4 * np.max(np.abs(ref))
+
+
+def test_es_fourier_matches_discrete_sum():
+    # the continuous transform of the ES kernel: a fine Riemann sum agrees
+    nf = 32
+    ph = mesh.es_fourier(nf)
+    t = np.linspace(-2.5, 2.5, 200001)
+    for m in (0, 3, 8, 15):
+        val = np.trapezoid(mesh.es_kernel(t) * np.cos(2 * np.pi * m / nf * t), t)
+        assert ph[m] == pytest.approx(val, rel=1e-8)
