@@ -371,6 +371,35 @@ def jvp_benchmark(dev, reps=5):
             "particle_steps_per_s_with_tangent": n ** 3 * 10 / (ms / 1e3), "ms_per_pk_jvp_host_timed": ms_pk}
 
 
+def nufft_benchmark(dev, reps=3):
+    """NUFFT force (ES kernel, width 5, grid upsampled twice, exact kernels) at
+    256^3 particles with a 256^3 band (512^3 internal grid): ICs + 6 steps."""
+    import numpy as np
+    import torch
+    from paper_2510_05206_gb300 import PM, Config
+    n = 256
+    pm = PM(Config(n_part=n, n_mesh=n, box=500.0, n_steps=6, grad_order=0, nufft=1), device=dev)
+    rng = np.random.default_rng(NOISE_SEED)
+    noise = torch.from_numpy(rng.standard_normal((1, n ** 3), dtype=np.float32)).to(dev)
+    d, v = pm.new_state()
+    for _ in range(2):
+        pm.ic_zeldovich(noise, d, v)
+        pm.run(d, v)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        pm.ic_zeldovich(noise, d, v)
+        pm.run(d, v)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    pm.close()
+    return {"workload": "pm_256cubed_nufft_band256_grid512_6step", "ms_per_run": ms, "ms_per_pm_step": ms / 6,
+            "particle_steps_per_s": n ** 3 * 6 / (ms / 1e3)}
+
+
 def lpt2_ic_benchmark(dev, reps=3):
     """2LPT initial conditions for the 512^3 lattice (four spectral chains and
     the source products) against the Zel'dovich ICs of the same handle size."""
@@ -569,6 +598,7 @@ def main():
         line["deconvolve"] = deconvolve_benchmark(dev)
         line["lpt2_ic"] = lpt2_ic_benchmark(dev)
         line["jvp"] = jvp_benchmark(dev)
+        line["nufft"] = nufft_benchmark(dev)
     if not args.no_serving:
         line["serving"] = serving_benchmark(args.serve_requests, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

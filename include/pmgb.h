@@ -71,6 +71,12 @@ typedef struct pm_config {
     int32_t lpt_order;   /* initial conditions: 1 = Zel'dovich (default, also 0), 2 = 2LPT
                             (Sec. 2.2, Eq. LPT at n = 2 with D^n growth: Psi = D psi1 + D^2 psi2,
                             V = psi1 + 2 D psi2; Table 4 `nlpt_order_ics`) */
+    int32_t nufft;       /* 1 = force by the NUFFT (Sec. 2.5): exponential-of-semicircle kernel of
+                            width 5 (5^3 taps) on a grid of 2 n_mesh cells per dimension, modes
+                            |m| < n_mesh/2 per axis, deconvolved by the kernel's transform twice;
+                            `order` is then unused and grad_order = lap_order = 0 (exact kernels),
+                            interlace = deconvolve = 0 are required; forward only (no adjoint,
+                            JVP or stage calls); default 0 */
 } pm_config;
 
 /* Fills *cfg with the defaults: CIC, no interlacing, 4th-order gradient, exact

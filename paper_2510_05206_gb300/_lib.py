@@ -22,7 +22,7 @@ class PmConfig(ctypes.Structure):
         ("omega_m", c_double), ("h", c_double), ("n_s", c_double), ("sigma8", c_double),
         ("a_ini", c_double), ("a_end", c_double), ("n_steps", c_int32), ("stepper", c_int32),
         ("time_var", c_int32), ("zero_corner", c_int32), ("batch", c_int32), ("pk_mesh_max", c_int32),
-        ("deconvolve", c_int32), ("lpt_order", c_int32),
+        ("deconvolve", c_int32), ("lpt_order", c_int32), ("nufft", c_int32),
     ]
 
 

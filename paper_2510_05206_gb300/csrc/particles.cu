@@ -13,8 +13,8 @@ namespace {
 // s cells, for a mesh 2^dshift times finer than the lattice (dshift may be < 0).
 struct AxisTaps {
     int c;       // first tap cell (unwrapped)
-    float w[4];  // weights of taps c, c+1 (CIC), c .. c+2 (TSC) or c .. c+3 (PCS)
-    float dw[4]; // d w / d u (u = position in cells), one-sided at CIC kinks as the floor gives
+    float w[5];  // weights of taps c, c+1 (CIC), c .. c+2 (TSC), c .. c+3 (PCS) or c .. c+4 (ES, NUFFT)
+    float dw[5]; // d w / d u (u = position in cells), one-sided at CIC kinks as the floor gives
 };
 
 template <int ORDER>
@@ -42,6 +42,20 @@ __device__ __forceinline__ AxisTaps axis_taps(int il, int dshift, float s) {
         a.dw[0] = -1.f;
         a.dw[1] = 1.f;
         a.dw[2] = 0.f;
+    } else if (ORDER == 5) {
+        // ES kernel of the NUFFT force (width 5, beta = 2.3 * 5): nearest node i0 =
+        // floor(t + 1/2), taps i0-2 .. i0+2, weight exp(beta (sqrt(1 - z^2) - 1)) with
+        // z = 2 x / 5 at distance x = cell - t (no derivatives: forward only)
+        const float fl = floorf(t + 0.5f);
+        a.c = base + (int)fl - 2;
+#pragma unroll
+        for (int o = 0; o < 5; ++o) {
+            const float z = 0.4f * (fl + (float)(o - 2) - t);
+            const float r = 1.f - z * z;
+            a.w[o] = r >= 0.f ? expf(11.5f * (sqrtf(r) - 1.f)) : 0.f;
+            a.dw[o] = 0.f;
+        }
+        return a;
     } else if (ORDER == 4) {
         // PCS (Table 1, cubic B-spline): cells floor(t)-1 .. floor(t)+2 at distances
         // 1+d, d, 1-d, 2-d (d = t - floor(t)); dw/du = -W'(x) at x = cell - u
@@ -403,6 +417,9 @@ __global__ void __launch_bounds__(256, 4) k_deposit_tiled(PmGeom g, const float*
 // X_half' - q = X + (tau2 + tau1') V' instead of X' - q.
 constexpr int IK_PPT = 2;
 
+// particles per thread of k_interp_kick: one for the wide kernels (PCS, ES)
+__host__ __device__ constexpr int ik_ppt(int order) { return order >= 4 ? 1 : IK_PPT; }
+
 template <int ORDER, int IL>
 __global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict__ disp, float* __restrict__ vel,
                                                      const SlotCoef* __restrict__ coef, int cstride,
@@ -414,7 +431,8 @@ __global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict
     const float tin = predrift_in ? 0.f : cf.tau1;
     const float tout = cf.tau2 + (coef_next ? coef_next[slot * cstride].tau1 : 0.f);
     const int N = 1 << (3 * g.log2np);                  // at most 2^30 particles per slot
-    const int i0 = blockIdx.x * (256 * IK_PPT) + threadIdx.x;
+    constexpr int PPT = ik_ppt(ORDER);
+    const int i0 = blockIdx.x * (256 * PPT) + threadIdx.x;
     float* dx = disp + slot * g.slot_part;
     float* dy = dx + N;
     float* dz = dy + N;
@@ -424,10 +442,10 @@ __global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict
     const int ds = g.log2ng - g.log2np, l2p = g.log2np, mp = (1 << l2p) - 1;
     const float4* f = force4 + slot * g.slot_mesh;
     const long long M = 1ll << (3 * g.log2ng);
-    float p[IK_PPT][3], u[IK_PPT][3], acc[IK_PPT][3];
+    float p[PPT][3], u[PPT][3], acc[PPT][3];
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-        for (int k = 0; k < IK_PPT; ++k) {
+        for (int k = 0; k < PPT; ++k) {
             const long long ip = (long long)i0 + 256 * k + STATE_PREFETCH;
             if (ip < N) {
                 prefetch_l2(dx + ip);
@@ -440,7 +458,7 @@ __global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict
         }
     }
 #pragma unroll
-    for (int k = 0; k < IK_PPT; ++k) {
+    for (int k = 0; k < PPT; ++k) {
         const int i = i0 + 256 * k;
         const bool ok = i < N;
         // the state is touched once per step: stream it past the caches the gathers use
@@ -454,7 +472,7 @@ __global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict
         for (int c = 0; c < 3; ++c) acc[k][c] = 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < IK_PPT; ++k) {
+    for (int k = 0; k < PPT; ++k) {
         const int i = i0 + 256 * k;
         if (i >= N) continue;
         const int ix = i & mp, iy = (i >> l2p) & mp, iz = i >> (2 * l2p);
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(256) k_interp_kick(PmGeom g, float* __restrict
         }
     }
 #pragma unroll
-    for (int k = 0; k < IK_PPT; ++k) {
+    for (int k = 0; k < PPT; ++k) {
         const int i = i0 + 256 * k;
         if (i >= N) continue;
         float vn[3];
@@ -1247,6 +1265,8 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
         k_deposit<3><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho);
     else if (order == 4)
         k_deposit<4><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho);
+    else if (order == 5)
+        k_deposit<5><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, shift_cells, rho);
     else
         return -1;
     return 0;
@@ -1261,7 +1281,8 @@ int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float
         k_interp_col<2><<<gt, 256, 0, st>>>(g, disp, vel, coef, coef_stride, force4, predrift_in, coef_next);
         return 0;
     }
-    dim3 grid((unsigned)((N + 256 * IK_PPT - 1) / (256 * IK_PPT)), nslots);
+    const int ppt = ik_ppt(order);
+    dim3 grid((unsigned)((N + 256 * ppt - 1) / (256 * ppt)), nslots);
 #define PM_IK(O, I) k_interp_kick<O, I><<<grid, 256, 0, st>>>(g, disp, vel, coef, coef_stride, force4, predrift_in, coef_next)
     if (order == 2 && !interlace) PM_IK(2, 0);
     else if (order == 2 && interlace) PM_IK(2, 1);
@@ -1269,6 +1290,7 @@ int pm_interp_kick(int order, int interlace, const PmGeom& g, float* disp, float
     else if (order == 3 && interlace) PM_IK(3, 1);
     else if (order == 4 && !interlace) PM_IK(4, 0);
     else if (order == 4 && interlace) PM_IK(4, 1);
+    else if (order == 5 && !interlace) PM_IK(5, 0);
     else return -1;
 #undef PM_IK
     return 0;

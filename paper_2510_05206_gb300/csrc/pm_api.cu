@@ -41,6 +41,7 @@ struct pm_handle {
     cudaStream_t stream = nullptr;
     int B = 1, np = 0, ng = 0, npk = 0, nmax = 0;
     int ngrids = 1, ncomp = 3;
+    int mak = 2;                 // mass assignment kernel of deposit and interpolation (5 = ES, NUFFT)
     std::unique_ptr<pmcosmo::Growth> growth;
     std::vector<pmcosmo::StepCoef> table;
     std::string err;
@@ -171,6 +172,12 @@ int validate(const pm_config* c, std::string& why) {
     if (c->interlace != 0 && c->interlace != 1) return bad("interlace must be 0 or 1");
     if (c->deconvolve != 0 && c->deconvolve != 1) return bad("deconvolve must be 0 or 1");
     if (c->lpt_order < 0 || c->lpt_order > 2) return bad("lpt_order must be 0, 1 (Zel'dovich) or 2 (2LPT)");
+    if (c->nufft != 0 && c->nufft != 1) return bad("nufft must be 0 or 1");
+    if (c->nufft) {
+        if (c->grad_order != 0 || c->lap_order != 0) return bad("nufft needs the exact kernels (grad_order = lap_order = 0)");
+        if (c->interlace || c->deconvolve) return bad("nufft excludes interlace and deconvolve");
+        if (2 * c->n_mesh > 1024) return bad("nufft: the upsampled grid 2 n_mesh must be <= 1024");
+    }
     for (int o : {c->grad_order, c->lap_order})
         if (o != 0 && o != 2 && o != 4 && o != 6) return bad("grad_order / lap_order must be 0, 2, 4 or 6");
     if (!(c->omega_m > 0 && c->omega_m <= 1)) return bad("omega_m must be in (0, 1]");
@@ -190,7 +197,8 @@ int validate(const pm_config* c, std::string& why) {
 }
 
 size_t workspace_bytes(const pm_config* c) {
-    const int ng = c->n_mesh, np = c->n_part, npk = c->pk_mesh_max ? c->pk_mesh_max : c->n_mesh;
+    const int ng = c->nufft ? 2 * c->n_mesh : c->n_mesh, np = c->n_part;
+    const int npk = c->pk_mesh_max ? c->pk_mesh_max : c->n_mesh;
     const int nmax = std::max(ng, std::max(np, npk));
     const int ngrids = c->interlace ? 2 : 1, ncomp = c->interlace ? 6 : 3;
     size_t b = 0;
@@ -323,7 +331,7 @@ int one_step(pm_handle* h, float* disp, float* vel, const SlotCoef* coef, int cs
     const PmGeom gd = geom(h, h->ng, h->rho_slot());
     h->phase(0, h->ngrids);
     for (int g = 0; g < h->ngrids; ++g)
-        pm_deposit(h->cfg.order, gd, disp, vel, coef, cstride, 0.5f * g, h->rho + g * Mg, h->B, st);
+        pm_deposit(h->mak, gd, disp, vel, coef, cstride, 0.5f * g, h->rho + g * Mg, h->B, st);
     h->phase_end();
     // delta = rho M/N - 1; the -1 only touches k = 0 (zeroed), and M/N with the
     // 1/M of the inverse transform leaves 1/N on the multiplier
@@ -331,7 +339,7 @@ int one_step(pm_handle* h, float* disp, float* vel, const SlotCoef* coef, int cs
     if (rc) return rc;
     const PmGeom gi = geom(h, h->ng, (long long)h->ngrids * Mg);
     h->phase(6, 1);
-    pm_interp_kick(h->cfg.order, h->cfg.interlace, gi, disp, vel, coef, cstride, h->force, h->B, st);
+    pm_interp_kick(h->mak, h->cfg.interlace, gi, disp, vel, coef, cstride, h->force, h->B, st);
     h->phase_end();
     return h->check_launch("pm step");
 }
@@ -495,7 +503,8 @@ int pm_init(const pm_config* cfg, void* stream, pm_handle** out) {
     h->stream = (cudaStream_t)stream;
     h->B = cfg->batch;
     h->np = cfg->n_part;
-    h->ng = cfg->n_mesh;
+    h->ng = cfg->nufft ? 2 * cfg->n_mesh : cfg->n_mesh;   // NUFFT: meshes on the upsampled grid
+    h->mak = cfg->nufft ? 5 : cfg->order;
     h->npk = cfg->pk_mesh_max ? cfg->pk_mesh_max : cfg->n_mesh;
     h->nmax = std::max(h->ng, std::max(h->np, h->npk));
     h->ngrids = cfg->interlace ? 2 : 1;
@@ -554,7 +563,37 @@ int pm_init(const pm_config* cfg, void* stream, pm_handle** out) {
         if ((rc = dalloc(h.get(), &h->d_grad, n, "gradient kernel"))) return bail(rc);
         cudaMemcpy(h->d_lap, lap.data(), n * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(h->d_grad, grad.data(), n * sizeof(float), cudaMemcpyHostToDevice);
-        if (cfg->deconvolve) {
+        if (cfg->nufft) {
+            // NUFFT: 1 / psi^(k)^2 per axis on the upsampled grid's bins, psi^ the continuous
+            // transform of the ES kernel (width 5, beta = 11.5; Simpson in FP64), and zero
+            // outside the band |m| < n_mesh / 2
+            const int nb = cfg->n_mesh;
+            const int q = 20000;                                  // Simpson intervals on [-2.5, 2.5]
+            std::vector<double> phi(q + 1);
+            for (int i = 0; i <= q; ++i) {
+                const double t = -2.5 + 5.0 * i / q, z = t / 2.5, r = 1.0 - z * z;
+                phi[i] = r > 0 ? std::exp(11.5 * (std::sqrt(r) - 1.0)) : (r == 0 ? std::exp(-11.5) : 0.0);
+            }
+            std::vector<float> dec(n);
+            for (int j = 0; j < n; ++j) {
+                const int m = j < n / 2 ? j : j - n;
+                if (std::abs(m) >= nb / 2) {
+                    dec[j] = 0.f;
+                    continue;
+                }
+                const double kap = 2.0 * M_PI * m / n;
+                double sum = 0;
+                for (int i = 0; i <= q; ++i) {
+                    const double t = -2.5 + 5.0 * i / q;
+                    const double wgt = (i == 0 || i == q) ? 1.0 : (i % 2 ? 4.0 : 2.0);
+                    sum += wgt * phi[i] * std::cos(kap * t);
+                }
+                const double ph = sum * (5.0 / q) / 3.0;
+                dec[j] = (float)(1.0 / (ph * ph));
+            }
+            if ((rc = dalloc(h.get(), &h->d_dec, n, "nufft deconvolution"))) return bail(rc);
+            cudaMemcpy(h->d_dec, dec.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+        } else if (cfg->deconvolve) {
             // Table 1: W^ = sinc^p(kt/2), sinc(x) = sin(pi x)/(pi x), kt = k/k_Ny = 2 m / n;
             // the deposit and the interpolation each apply it once: divide by W^2
             std::vector<float> dec(n);
@@ -718,15 +757,15 @@ int pm_run(pm_handle* h, float* disp, float* vel, int32_t b, int32_t e) {
             return h->fail(PM_ERR_CUDA, "memset density");
         h->phase(0, 1);
         if (s == b)
-            pm_deposit(h->cfg.order, gd, disp, vel, h->d_table + s, 0, 0.f, h->rho, h->B, st);
+            pm_deposit(h->mak, gd, disp, vel, h->d_table + s, 0, 0.f, h->rho, h->B, st);
         else
-            pm_deposit(h->cfg.order, gd, disp, nullptr, h->d_unit, 0, 0.f, h->rho, h->B, st);
+            pm_deposit(h->mak, gd, disp, nullptr, h->d_unit, 0, 0.f, h->rho, h->B, st);
         h->phase_end();
         int rc = spectral_force(h, h->rho, h->rho_slot(), Mg, (float)(1.0 / (double)h->Np()), nullptr, h->force, h->B,
                                 s + 1 < e);
         if (rc) return rc;
         h->phase(6, 1);
-        pm_interp_kick(h->cfg.order, 0, gf, disp, vel, h->d_table + s, 0, h->force, h->B, st, s > b,
+        pm_interp_kick(h->mak, 0, gf, disp, vel, h->d_table + s, 0, h->force, h->B, st, s > b,
                        s + 1 < e ? h->d_table + s + 1 : nullptr);
         h->phase_end();
         if ((rc = h->check_launch("pm_run step"))) return rc;
@@ -889,6 +928,7 @@ int pm_density(pm_handle* h, const float* disp, int32_t n, int32_t order, float*
 }
 
 int pm_force_mesh(pm_handle* h, const float* delta, float* force) {
+    if (h && h->cfg.nufft) return h->fail(PM_ERR_UNSUPPORTED, "pm_force_mesh: not available with the NUFFT force");
     if (!h) return PM_ERR_ARG;
     if (!delta || !force) return h->fail(PM_ERR_ARG, "pm_force_mesh: NULL buffer");
     if (h->ngrids != 1) return h->fail(PM_ERR_UNSUPPORTED, "pm_force_mesh: single grid only");
@@ -896,6 +936,7 @@ int pm_force_mesh(pm_handle* h, const float* delta, float* force) {
 }
 
 int pm_interp(pm_handle* h, const float* disp, const float* force, float* acc) {
+    if (h && h->cfg.nufft) return h->fail(PM_ERR_UNSUPPORTED, "pm_interp: not available with the NUFFT force");
     if (!h) return PM_ERR_ARG;
     if (!disp || !force || !acc) return h->fail(PM_ERR_ARG, "pm_interp: NULL buffer");
     if (h->ngrids != 1) return h->fail(PM_ERR_UNSUPPORTED, "pm_interp: single grid only");
@@ -920,6 +961,7 @@ int adj_alloc(pm_handle* h) {
 }  // namespace
 
 int pm_jvp(pm_handle* h, float* disp, float* vel, float* tdisp, float* tvel, int32_t b, int32_t e) {
+    if (h && h->cfg.nufft) return h->fail(PM_ERR_UNSUPPORTED, "pm_jvp: not available with the NUFFT force");
     if (!h) return PM_ERR_ARG;
     if (!disp || !vel || !tdisp || !tvel) return h->fail(PM_ERR_ARG, "pm_jvp: NULL buffer");
     if (h->ngrids != 1) return h->fail(PM_ERR_UNSUPPORTED, "pm_jvp: interlaced grids are not supported");
@@ -951,6 +993,7 @@ int pm_jvp(pm_handle* h, float* disp, float* vel, float* tdisp, float* tvel, int
 }
 
 int pm_adjoint(pm_handle* h, float* disp, float* vel, float* adisp, float* avel, int32_t step_end) {
+    if (h && h->cfg.nufft) return h->fail(PM_ERR_UNSUPPORTED, "pm_adjoint: not available with the NUFFT force");
     if (!h) return PM_ERR_ARG;
     if (!disp || !vel || !adisp || !avel) return h->fail(PM_ERR_ARG, "pm_adjoint: NULL buffer");
     if (h->ngrids != 1) return h->fail(PM_ERR_UNSUPPORTED, "pm_adjoint: interlaced grids are not supported");
@@ -1064,6 +1107,7 @@ int pm_ic_adjoint(pm_handle* h, const float* noise, const float* adisp, const fl
 }
 
 int pm_density_vjp(pm_handle* h, const float* disp, int32_t n, int32_t order, const float* ddelta, float* adisp) {
+    if (h && h->cfg.nufft) return h->fail(PM_ERR_UNSUPPORTED, "pm_density_vjp: not available with the NUFFT force");
     if (!h) return PM_ERR_ARG;
     if (!disp || !ddelta || !adisp) return h->fail(PM_ERR_ARG, "pm_density_vjp: NULL buffer");
     if (!pow2_in_range(n)) return h->fail(PM_ERR_ARG, "mesh %d must be a power of two in [16, 1024]", n);

@@ -33,6 +33,7 @@ class Config:
     pk_mesh_max: int = 0
     deconvolve: int = 0         # divide the force density by the squared kernel (Table 1 W^)
     lpt_order: int = 1          # initial conditions: 1 = Zel'dovich, 2 = 2LPT
+    nufft: int = 0              # force by the NUFFT (ES kernel on a 2 n_mesh grid, n_mesh band)
 
     def to_c(self):
         c = _lib.PmConfig()

@@ -284,3 +284,28 @@ def test_invalid_calls_raise():
         pm.step(d, v, 99)
     with pytest.raises(RuntimeError):
         pm.power_spectrum(d, 2048, 8)
+
+
+@pytest.mark.parametrize("n_part,n_mesh", [(16, 16), (32, 16), (16, 32)])
+def test_nufft_run_parity(n_part, n_mesh):
+    # NUFFT force (ES kernel, width 5, grid 2 n_mesh, n_mesh band) against the
+    # oracle's FP64 NUFFT (itself within ~1e-4 of the exact band-limited DFT)
+    kw = dict(n_part=n_part, n_mesh=n_mesh, box=64.0, n_steps=3, grad_order=0)
+    pm = PM(Config(nufft=1, **kw), device=DEV)
+    w = inputs.white_noise(n_part, seed=51)
+    d, v = pm.ic_zeldovich(_t(w.reshape(1, -1)))
+    pm.run(d, v)
+    ocfg = nbody.Config(nufft=True, **kw)
+    P0, V0 = nbody.zeldovich_ic(ocfg, w)
+    P1, V1 = nbody.run(ocfg, P0, V0)
+    assert _disp_err(_np(d)[0], P1) < 1e-4
+    assert _disp_err(_np(v)[0], V1) < 1e-4
+
+
+def test_nufft_rejects_unsupported_calls():
+    pm = PM(Config(n_part=16, n_mesh=16, box=64.0, grad_order=0, nufft=1), device=DEV)
+    d, v = pm.new_state()
+    with pytest.raises(RuntimeError):
+        pm.adjoint(d, v, torch.zeros_like(d), torch.zeros_like(v))
+    with pytest.raises(RuntimeError):
+        PM(Config(n_part=16, n_mesh=16, box=64.0, grad_order=4, nufft=1), device=DEV)
