@@ -16,7 +16,8 @@ It restates, step by step and in double precision, what the paper
   their position derivatives (App. C), finite-difference gradient and
   Laplacian kernels (Table 2), the Poisson force field (Sec. 2.5, Eq. poisson)
   with optional deconvolution by the squared kernel (Sec. 2.5, Table 1),
-  interlacing, and the binned power spectrum.
+  the NUFFT force (ES kernel on an upsampled grid), interlacing, and the
+  binned power spectrum.
 * ``nbody``      - Zel'dovich and 2LPT initial conditions (Sec. 2.2, Eqs. LPT,
   helmholtz, LPT_L_and_T), the DKD stepper (Eq. dkd), full runs, the
   adjoint method (Sec. 2.7, Table 5, App. C) and its forward-mode counterpart
