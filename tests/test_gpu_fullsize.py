@@ -108,3 +108,40 @@ def test_adjoint_workload_central_differences_64_directions():
     assert np.max(err) < 1e-1, np.sort(err)
     assert np.corrcoef(adj, fds)[0, 1] > 0.99
     pm.close()
+
+
+def test_zero_noise_stays_on_the_lattice():
+    # degenerate input: an unperturbed lattice deposits delta = 0 exactly (mesh = lattice,
+    # corner placement), so the force, the velocities and the displacements stay zero
+    for n, ng, order in ((32, 32, 2), (32, 64, 3), (16, 16, 4)):
+        pm = PM(Config(n_part=n, n_mesh=ng, box=100.0, order=order, n_steps=4), device=DEV)
+        d, v = pm.ic_zeldovich(torch.zeros((1, n ** 3), device=DEV))
+        pm.run(d, v)
+        assert float(d.abs().max()) == 0.0 and float(v.abs().max()) == 0.0
+        pm.close()
+
+
+@pytest.mark.slow
+def test_maximum_size_1024_conservation():
+    # the largest supported size (1024^3 particles on a 1024^3 mesh, ~45 GB on the
+    # device): no oracle at this size, so properties that hold at any size --
+    # finite state, mass conservation of the deposit, and momentum conservation of
+    # the PM force (the total velocity change of a step is round-off)
+    n, L = 1024, 2000.0
+    pm = PM(Config(n_part=n, n_mesh=n, box=L, n_steps=6), device=DEV)
+    g = torch.Generator(device=DEV)
+    g.manual_seed(5)
+    noise = torch.randn((1, n ** 3), generator=g, device=DEV)
+    d, v = pm.ic_zeldovich(noise)
+    del noise
+    delta = pm.density(d)
+    assert abs(float(delta.double().sum())) < 1e-6 * n ** 3
+    del delta
+    v0 = v.clone()
+    pm.step(d, v, 0)
+    assert bool(torch.isfinite(d).all()) and bool(torch.isfinite(v).all())
+    dv = (v.double() - v0.double())
+    tot = dv.sum(dim=2).abs().max().item()
+    scale = dv.abs().sum(dim=2).max().item()
+    assert tot < 1e-4 * scale
+    pm.close()
