@@ -152,8 +152,9 @@ __device__ __forceinline__ void stage_load(const Ld& ld, float2 v[8], bool activ
     }
 }
 
-// The twiddles, butterflies and stores of one stage on loaded values v.
-template <int N, int R, int NS, int NL, int DIR, class St>
+// The twiddles, butterflies and stores of one stage on loaded values v (STORE =
+// false: the results stay in v, butterfly b's outputs r at v[b R + r]).
+template <int N, int R, int NS, int NL, int DIR, class St, bool STORE = true>
 __device__ __forceinline__ void stage_cs(float2 v[8], const St& st, const float2* tw, int twstride, bool active) {
     constexpr int NB = 8 / R;
     const int line = threadIdx.x % NL;
@@ -171,9 +172,11 @@ __device__ __forceinline__ void stage_cs(float2 v[8], const St& st, const float2
             if (R == 8) dft8<DIR>(vb);
             if (R == 4) dft4<DIR>(vb[0], vb[1], vb[2], vb[3]);
             if (R == 2) dft2<DIR>(vb[0], vb[1]);
-            const int o = (jj / NS) * NS * R + k;
+            if (STORE) {
+                const int o = (jj / NS) * NS * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) st(line, o + r * NS, vb[r]);
+                for (int r = 0; r < R; ++r) st(line, o + r * NS, vb[r]);
+            }
         }
     }
 }
@@ -246,6 +249,44 @@ __device__ __forceinline__ void fft_pre(float2 v[8], const St& st, const Sm& sm,
         __syncthreads();
     }
     stage_io<N, Pl::radix(Pl::S - 1), Pl::ns(Pl::S - 1), NL, DIR, LAST_SMEM>(sm, st, tw, twstride, active);
+}
+
+// All stages but the last of an N-point transform: the first reads `ld`, the
+// others work in place on `sm`; ends with a barrier, the data in `sm`.
+template <int N, int NL, int DIR, class Ld, class Sm>
+__device__ __forceinline__ void fft_head(const Ld& ld, const Sm& sm, const float2* tw, int twstride) {
+    using Pl = Plan<N>;
+    const bool active = threadIdx.x < NL * N / 8;
+    stage_io<N, Pl::radix(0), 1, NL, DIR, false>(ld, sm, tw, twstride, active);
+    __syncthreads();
+    if constexpr (Pl::S > 2) {
+        stage_io<N, Pl::radix(1), Pl::ns(1), NL, DIR, true>(sm, sm, tw, twstride, active);
+        __syncthreads();
+    }
+    if constexpr (Pl::S > 3) {
+        stage_io<N, Pl::radix(2), Pl::ns(2), NL, DIR, true>(sm, sm, tw, twstride, active);
+        __syncthreads();
+    }
+}
+
+// The last stage after fft_head, into registers: out[r'] = element j + r' N/8 of
+// line l (thread = (l, j) = (tid % NL, tid / NL)), the order in which the first
+// stage of another transform (fft_pre) takes its inputs.  The last stage of
+// radix R leaves butterfly b's output r at element j + b N/8 + r N/R, i.e. r' =
+// b + r 8/R.
+template <int N, int NL, int DIR, class Sm>
+__device__ __forceinline__ void fft_tail_regs(const Sm& sm, float2 out[8], const float2* tw, int twstride) {
+    using Pl = Plan<N>;
+    constexpr int R = Pl::radix(Pl::S - 1), NS = Pl::ns(Pl::S - 1), NB = 8 / R;
+    static_assert(NS * R == N, "last stage");
+    const bool active = threadIdx.x < NL * N / 8;
+    float2 v[8];
+    stage_load<N, R, NL>(sm, v, active);
+    stage_cs<N, R, NS, NL, DIR, Sm, false>(v, sm, tw, twstride, active);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[b + r * NB] = v[b * R + r];
 }
 
 // Shared-memory column tile of NL = COL_TILE columns: element e of column l at

@@ -282,6 +282,29 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
         return;
     }
 
+    if constexpr (MODE == Z_POT) {
+        // potential phi^ = scale * delta^ / K_lap(k): the forward transform's last stage
+        // leaves each thread the elements the inverse's first stage takes, so the
+        // multiplier is applied in registers between them (no shared-memory round trip)
+        fft_head<n, COL_TILE, -1>(in0, A, tw, 1);
+        float2 v[8];
+        fft_tail_regs<n, COL_TILE, -1>(A, v, tw, 1);
+        const int l = threadIdx.x % COL_TILE, j = threadIdx.x / COL_TILE;
+        const int kx = kx0 + l;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int e = j + r * (n / 8);
+            float f = 0.f;
+            if (kx <= n / 2 && (kx | y | e) != 0) {
+                f = a.scale / (lap[kx] + lap[y] + lap[e]);
+                if constexpr (deconv) f *= dec[kx] * dec[y] * dec[e];
+            }
+            v[r] = cscale(v[r], f);
+        }
+        fft_pre<n, COL_TILE, 1, false>(v, GCols{a.out[0] + off, ES}, B, tw, 1);
+        return;
+    }
+
     fft_io<n, COL_TILE, -1, false, true>(in0, A, A, tw, 1);
     if (MODE == Z_FORCE_IL || MODE == Z_POT_IL || MODE == Z_PKX) {
         __syncthreads();
