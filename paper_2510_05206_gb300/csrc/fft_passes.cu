@@ -169,6 +169,11 @@ __global__ void __launch_bounds__(768) k_fft_x_c2r3(const float2* __restrict__ i
 // reads it straight from global memory and the last stage writes it straight
 // back (fft_io), so a tile makes two shared-memory round trips per element for
 // n = 512 instead of four.
+// y rows per CTA of the P(k) z pass (amortises its accumulator clear / reduce / flush;
+// the forward-mode pass, with two transforms per row, keeps one row to stay in registers)
+__host__ __device__ constexpr int z_pk_rows(int log2n, bool two) {
+    return two ? 1 : (log2n >= 9 ? 8 : (log2n == 8 ? 2 : 1));
+}
 __host__ __device__ constexpr int col_min_blocks(int log2n) { return (1024 >> log2n) > 32 ? 32 : ((1024 >> log2n) < 1 ? 1 : (1024 >> log2n)); }
 
 // y pass: grid (tile groups, n planes, meshes).  A CTA transforms Y_TPC column
@@ -245,6 +250,77 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
             if (deconv) dec[i] = a.dec1[i];
         }
     }
+    if constexpr (MODE == Z_PK || MODE == Z_PKX) {
+        // sum over the modes of each bin of w |delta^|^2 (w = 2 for 0 < kx < n/2, the
+        // half spectrum standing for +-kx), FP64 per bin; Z_PKX (forward mode of P(k))
+        // sums w 2 Re(conj(delta^) delta'^) with delta'^ the transform of in[1].
+        // A CTA takes the same kx columns of ROWS consecutive y rows, so its
+        // accumulators are cleared, reduced and flushed once for all of them: runs of
+        // equal bin along kz are summed per thread in FP32, added to per-warp (or one
+        // shared set of) FP64 accumulators in shared memory, and each CTA adds its
+        // non-zero bins to the output with one global atomic each.  Mode counts and
+        // mean |k| per bin depend on the mesh only and are tabulated on the host.
+        double* acc = reinterpret_cast<double*>(B.s);
+        constexpr int NW = (1 << LOG2N) >= 32 ? (1 << LOG2N) / 32 : 1;
+        const bool priv = NW * a.nbins <= TE;
+        const int nacc = priv ? NW * a.nbins : a.nbins;
+        for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0.0;
+        __syncthreads();
+        double* wacc = priv ? acc + (threadIdx.x >> 5) * a.nbins : acc;
+        const int slot = blockIdx.z;
+        const int kx0 = blockIdx.x * COL_TILE;
+        // thread: column l, COL_TILE consecutive kz planes.  Along a column |k| is monotone
+        // on each side of kz = n/2, so the bin changes rarely.
+        constexpr int CH = COL_TILE;                       // n * COL_TILE elements / n threads
+        const int l = threadIdx.x % COL_TILE, e0 = (threadIdx.x / COL_TILE) * CH;
+        const int kx = kx0 + l;
+        const float wx = (kx == 0 || kx == n / 2) ? 1.f : 2.f;
+        constexpr int ROWS = z_pk_rows(LOG2N, MODE == Z_PKX);
+#pragma unroll 1
+        for (int yy = 0; yy < ROWS; ++yy) {
+            const int y = blockIdx.y * ROWS + yy;
+            const long long off = slot * a.slot_stride + (long long)y * P + kx0;
+            const int my = freq_index(y, n);
+            fft_io<n, COL_TILE, -1, false, true>(GCols{const_cast<float2*>(a.in[0]) + off, ES}, A, A, tw, 1);
+            if (MODE == Z_PKX) {
+                __syncthreads();
+                fft_io<n, COL_TILE, -1, false, true>(GCols{const_cast<float2*>(a.in[1]) + off, ES}, A2, A2, tw, 1);
+            }
+            __syncthreads();
+            if (kx <= n / 2) {
+                const int kxy = kx * kx + my * my;
+                int cur = -1;
+                float run = 0.f;
+#pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    const int e = e0 + k, mz = freq_index(e, n);
+                    const int bk = __ldg(&a.bintab[kxy + mz * mz]);
+                    const float2 d = A(l, e);
+                    const float2 dt = MODE == Z_PKX ? A2(l, e) : d;
+                    if (bk != cur) {
+                        if (cur >= 0) atomicAdd(&wacc[cur], (double)run);
+                        cur = bk;
+                        run = 0.f;
+                    }
+                    run += (MODE == Z_PKX ? 2.f * wx : wx) * (d.x * dt.x + d.y * dt.y);
+                }
+                if (cur >= 0) atomicAdd(&wacc[cur], (double)run);
+            }
+            __syncthreads();   // the next row's transform overwrites A
+        }
+        if (priv)
+            for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+                double sum = 0.0;
+                for (int w = 0; w < NW; ++w) sum += acc[w * a.nbins + i];
+                acc[i] = sum;   // each i is owned by one thread: reading row 0 before writing it is safe
+            }
+        __syncthreads();
+        double* dst = a.pk_out + (long long)slot * a.nbins;
+        for (int i = threadIdx.x; i < a.nbins; i += blockDim.x)
+            if (acc[i] != 0.0) atomicAdd(&dst[i], acc[i]);
+        return;
+    }
+
     const int slot = blockIdx.z;
     const int y = blockIdx.y;
     const int kx0 = blockIdx.x * COL_TILE;
@@ -305,69 +381,32 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
         return;
     }
 
-    fft_io<n, COL_TILE, -1, false, true>(in0, A, A, tw, 1);
-    if (MODE == Z_FORCE_IL || MODE == Z_POT_IL || MODE == Z_PKX) {
+    if constexpr (MODE == Z_IC) {
+        // the factor kf T(k^2) that the three components share is applied once, between
+        // the forward transform's last stage (in registers) and its store to A; the
+        // components then only multiply by i m_c
+        fft_head<n, COL_TILE, -1>(in0, A, tw, 1);
+        float2 v[8];
+        fft_tail_regs<n, COL_TILE, -1>(A, v, tw, 1);
+        const int l = threadIdx.x % COL_TILE, j = threadIdx.x / COL_TILE;
+        const int kx = kx0 + l;
+        __syncthreads();   // every thread has read its last-stage inputs from A
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int e = j + r * (n / 8), mz = freq_index(e, n);
+            // zero on every Nyquist plane and in the padding columns
+            const float f = (kx < n / 2 && y != n / 2 && e != n / 2)
+                                ? a.kf * __ldg(&a.ictab[kx * kx + my * my + mz * mz]) : 0.f;
+            A(l, e, cscale(v[r], f));
+        }
+    } else {
+        fft_io<n, COL_TILE, -1, false, true>(in0, A, A, tw, 1);
+    }
+    if (MODE == Z_FORCE_IL || MODE == Z_POT_IL) {
         __syncthreads();
         fft_io<n, COL_TILE, -1, false, true>(GCols{const_cast<float2*>(a.in[1]) + off, ES}, A2, A2, tw, 1);
     }
     __syncthreads();
-
-    if (MODE == Z_PK || MODE == Z_PKX) {
-        // Z_PKX (forward mode of P(k)): the same sums of w 2 Re(conj(delta^) delta'^)
-        // with delta'^ the transform of in[1] (in A2).
-        // sum over the modes of each bin of w |delta^|^2 (w = 2 for 0 < kx < n/2, the
-        // half spectrum standing for +-kx), FP64 per bin: runs of equal bin along kz
-        // are summed per thread, then added to a per-warp (or shared) FP64 accumulator
-        // in shared memory, then one global atomic per bin and CTA.  Mode counts and
-        // mean |k| per bin depend on the mesh only and are tabulated exactly on the host.
-        // per-warp private FP64 accumulators when they fit (no contention between
-        // warps), else one shared set updated atomically
-        double* acc = reinterpret_cast<double*>(B.s);
-        constexpr int NW = (1 << LOG2N) >= 32 ? (1 << LOG2N) / 32 : 1;
-        const bool priv = NW * a.nbins <= TE;
-        const int nacc = priv ? NW * a.nbins : a.nbins;
-        for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0.0;
-        __syncthreads();
-        double* wacc = priv ? acc + (threadIdx.x >> 5) * a.nbins : acc;
-        // thread: column l, COL_TILE consecutive kz planes.  Along a column |k| is monotone
-        // on each side of kz = n/2, so the bin changes rarely: sum in FP32 while it stays,
-        // and add each finished run to the FP64 bin accumulator.
-        constexpr int CH = COL_TILE;                       // n * COL_TILE elements / n threads
-        const int l = threadIdx.x % COL_TILE, e0 = (threadIdx.x / COL_TILE) * CH;
-        const int kx = kx0 + l;
-        if (kx <= n / 2) {
-            const float wx = (kx == 0 || kx == n / 2) ? 1.f : 2.f;
-            const int kxy = kx * kx + my * my;
-            int cur = -1;
-            float run = 0.f;
-#pragma unroll
-            for (int k = 0; k < CH; ++k) {
-                const int e = e0 + k, mz = freq_index(e, n);
-                const int bk = __ldg(&a.bintab[kxy + mz * mz]);
-                const float2 d = A(l, e);
-                const float2 dt = MODE == Z_PKX ? A2(l, e) : d;
-                if (bk != cur) {
-                    if (cur >= 0) atomicAdd(&wacc[cur], (double)run);
-                    cur = bk;
-                    run = 0.f;
-                }
-                run += (MODE == Z_PKX ? 2.f * wx : wx) * (d.x * dt.x + d.y * dt.y);
-            }
-            if (cur >= 0) atomicAdd(&wacc[cur], (double)run);
-        }
-        __syncthreads();
-        if (priv)
-            for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
-                double sum = 0.0;
-                for (int w = 0; w < NW; ++w) sum += acc[w * a.nbins + i];
-                acc[i] = sum;   // each i is owned by one thread: reading row 0 before writing it is safe
-            }
-        __syncthreads();
-        double* dst = a.pk_out + (long long)slot * a.nbins;
-        for (int i = threadIdx.x; i < a.nbins; i += blockDim.x)
-            if (acc[i] != 0.0) atomicAdd(&dst[i], acc[i]);
-        return;
-    }
 
     if (MODE == Z_POT || MODE == Z_POT_IL) {
         // potential phi^ = scale * delta^ / K_lap(k) (k = 0 -> 0); the gradient of a
@@ -408,13 +447,9 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
             if (kx > n / 2) return r;
             const int mz = freq_index(e, n);
             if (MODE == Z_IC) {
-                // psi1_c^ = i k_c T(k^2) w^, zero on every Nyquist plane
-                if (kx != n / 2 && y != n / 2 && e != n / 2) {
-                    const int mc = axis == 0 ? kx : (axis == 1 ? my : mz);
-                    const float f = a.kf * (float)mc * __ldg(&a.ictab[kx * kx + my * my + mz * mz]);
-                    r = cmul_i(cscale(A(l, e), f), 1);
-                }
-                return r;
+                // psi1_c^ = i k_c T(k^2) w^ (A holds kf T w^, zero on every Nyquist plane)
+                const int mc = axis == 0 ? kx : (axis == 1 ? my : mz);
+                return cmul_i(cscale(A(l, e), (float)mc), 1);
             }
             if (MODE == Z_IC_D2 || MODE == Z_IC_O2) {
                 // second derivatives of psi1 for the 2LPT source (Eq. LPT_kernels):
@@ -534,7 +569,7 @@ void launch_z_mode(const ZArgs& a, int nslots, cudaStream_t st) {
     constexpr int M = MODE & (Z_DEC - 1);
     const int ntile = (M == Z_FORCE_IL || M == Z_ADJ || M == Z_IC_ADJ || M == Z_POT_IL || M == Z_PKX) ? 3 : 2;
     const size_t smem = (size_t)(ntile * col_tile_elems(n) + 2 * n + ((MODE & Z_DEC) ? n / 2 : 0)) * sizeof(float2);
-    dim3 grid(n / 2 / COL_TILE + 1, n, nslots);
+    dim3 grid(n / 2 / COL_TILE + 1, (M == Z_PK || M == Z_PKX) ? n / z_pk_rows(LOG2N, M == Z_PKX) : n, nslots);
     set_smem(k_fft_z<LOG2N, MODE>, smem);
     k_fft_z<LOG2N, MODE><<<grid, n, smem, st>>>(a);
 }
