@@ -47,12 +47,13 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []            # (host time of arrival, csv line)
+        self.window = (0.0, float("inf"))
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -61,7 +62,15 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def begin(self):
+        """Start of the timed region (the sampler runs from before the warm-up so that
+        nvidia-smi's start-up latency does not eat the region)."""
+        self.window = (time.perf_counter(), float("inf"))
+
+    def end(self):
+        self.window = (self.window[0], time.perf_counter())
 
     def stop(self):
         if not self.proc:
@@ -74,7 +83,9 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, smax, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if not self.window[0] <= ts <= self.window[1]:
+                continue
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -88,7 +99,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in the timed region"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
@@ -120,6 +131,25 @@ def measured_traffic(kernel):
                 return int(p[2])
             return None
     return None
+
+
+def host_link_gbs(host):
+    """Plain pinned-host <-> device copy rates of one state-sized buffer (context
+    for the end-to-end number: the host link differs between machines)."""
+    dev_buf = torch.empty(host.shape, dtype=host.dtype, device="cuda")
+    out = {}
+    for name, (dst, src) in (("h2d", (dev_buf, host)), ("d2h", (host, dev_buf))):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = 3 * host.numel() * host.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del dev_buf
+    return out
 
 
 def algorithmic_bytes(n_part, n_mesh, n_steps=6):
@@ -467,7 +497,7 @@ def deconvolve_benchmark(dev, reps=3):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -515,16 +545,17 @@ def main():
         pm.run(disp, vel)
         return pm.power_spectrum(disp, WORKLOAD["pk_mesh"], WORKLOAD["pk_bins"])
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(max(args.warmup, 3)):
         one_sim()
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
     pm.profile(True)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
@@ -532,6 +563,7 @@ def main():
         k, pk, cnt = one_sim()
     t1.record()
     torch.cuda.synchronize()
+    clocks.end()
     clock_info = clocks.stop()
     ms = t0.elapsed_time(t1)
     prof = pm.profile_read()
@@ -563,7 +595,7 @@ def main():
             e2e_s = float(t.item())
         e2e = {"value": N * cfg.n_steps * args.e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                "d2h_bytes_per_step": 2 * 3 * 4 * N, "steps": args.e2e_steps,
-               "ms_per_step": e2e_s * 1e3 / args.e2e_steps}
+               "ms_per_step": e2e_s * 1e3 / args.e2e_steps, "host_link_gbs": host_link_gbs(d_host)}
 
     # roofline of the dominant kernel (largest share of the timed region)
     alg = algorithmic_bytes(n, cfg.n_mesh, cfg.n_steps)
