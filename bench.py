@@ -133,6 +133,23 @@ def measured_traffic(kernel):
     return None
 
 
+def max_over_ranks(x, ws, dev):
+    """The largest x over the ranks (the slowest rank's time sets the job's)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, seconds):
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank runs its own replica of the workload)."""
+    return units_per_rank * ws / seconds
+
+
 def host_link_gbs(host):
     """Plain pinned-host <-> device copy rates of one state-sized buffer (context
     for the end-to-end number: the host link differs between machines)."""
@@ -568,13 +585,10 @@ def main():
     ms = t0.elapsed_time(t1)
     prof = pm.profile_read()
     pm.profile(False)
+    ms = max_over_ranks(ms, ws, dev)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    particle_steps = N * cfg.n_steps * args.steps * ws
-    value = particle_steps / (ms / 1e3)
+    value = whole_job_rate(N * cfg.n_steps * args.steps, ws, ms / 1e3)
 
     # end to end through the host-buffer C ABI call: pinned noise in, disp + vel out
     e2e = None
@@ -589,11 +603,8 @@ def main():
             pm.simulate_host(noise_host, d_host, v_host)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - te
-        if ws > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": N * cfg.n_steps * args.e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+        e2e_s = max_over_ranks(e2e_s, ws, dev)
+        e2e = {"value": whole_job_rate(N * cfg.n_steps * args.e2e_steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                "d2h_bytes_per_step": 2 * 3 * 4 * N, "steps": args.e2e_steps,
                "ms_per_step": e2e_s * 1e3 / args.e2e_steps, "host_link_gbs": host_link_gbs(d_host)}
 
