@@ -261,6 +261,42 @@ def test_slot_schedule_mixed_steps():
         assert _disp_err(_np(disp)[b], _np(d1)[0]) < 1e-5
 
 
+@pytest.mark.parametrize("n_steps", [1, 2])
+def test_shortest_runs_parity(n_steps):
+    # one step (no carried pre-drift) and two steps (the shortest run that carries it)
+    pm, disp, vel, P1, V1 = _run_pair(dict(n_part=32, n_mesh=32, box=256.0, n_steps=n_steps), seed=11)
+    assert _disp_err(_np(disp)[0], P1) < 1e-4
+    assert _disp_err(_np(vel)[0], V1) < 1e-4
+
+
+@pytest.mark.parametrize("cuts", [(3,), (1, 2, 5), (1, 2, 3, 4, 5)])
+def test_run_in_segments_equals_one_run(cuts):
+    # a run split into step ranges leaves the same state as one call: each call
+    # starts and ends on plain positions, whatever it carries between its steps
+    n, L = 32, 256.0
+    w = _t(inputs.white_noise(n, seed=12).reshape(1, -1))
+    pm = PM(Config(n_part=n, n_mesh=n, box=L), device=DEV)
+    d0, v0 = pm.ic_zeldovich(w)
+    pm.run(d0, v0)
+    d1, v1 = pm.ic_zeldovich(w)
+    edges = (0,) + cuts + (6,)
+    for b, e in zip(edges[:-1], edges[1:]):
+        pm.run(d1, v1, b, e)
+    # the split only regroups float additions of the drifts (X + t2 V + t1' V)
+    assert _disp_err(_np(d1)[0], _np(d0)[0]) < 1e-5
+    assert _disp_err(_np(v1)[0], _np(v0)[0]) < 1e-5
+
+
+def test_empty_step_range_is_a_no_op():
+    n = 16
+    pm = PM(Config(n_part=n, n_mesh=n, box=100.0), device=DEV)
+    d, v = pm.ic_zeldovich(_t(inputs.white_noise(n, seed=13).reshape(1, -1)))
+    d_ref, v_ref = d.clone(), v.clone()
+    pm.run(d, v, 3, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(d, d_ref) and torch.equal(v, v_ref)
+
+
 def test_simulate_host_matches_device_path():
     n, L = 32, 256.0
     pm = PM(Config(n_part=n, n_mesh=n, box=L), device=DEV)
