@@ -153,6 +153,7 @@ def whole_job_rate(units_per_rank, ws, seconds):
 def host_link_gbs(host):
     """Plain pinned-host <-> device copy rates of one state-sized buffer (context
     for the end-to-end number: the host link differs between machines)."""
+    import torch
     dev_buf = torch.empty(host.shape, dtype=host.dtype, device="cuda")
     out = {}
     for name, (dst, src) in (("h2d", (dev_buf, host)), ("d2h", (host, dev_buf))):
@@ -590,23 +591,37 @@ def main():
         dist.barrier()
     value = whole_job_rate(N * cfg.n_steps * args.steps, ws, ms / 1e3)
 
-    # end to end through the host-buffer C ABI call: pinned noise in, disp + vel out
-    e2e = None
+    # end to end through the host-buffer C ABI calls, every step from pinned host
+    # noise: (1) the same step as the device-timed one (ICs + run + P(k)) with the
+    # binned P(k) read back to the host; (2) ICs + run with the whole particle
+    # state (disp, vel) read back instead
+    e2e = e2e_state = None
     if args.e2e_steps > 0:
+        nb = WORKLOAD["pk_bins"]
+
+        def timed(call):
+            call()
+            if ws > 1:
+                dist.barrier()
+            te = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                call()
+            torch.cuda.synchronize()
+            return max_over_ranks(time.perf_counter() - te, ws, dev)
+
+        e2e_s = timed(lambda: pm.simulate_pk_host(noise_host, WORKLOAD["pk_mesh"], nb))
+        e2e = {"value": whole_job_rate(N * cfg.n_steps * args.e2e_steps, ws, e2e_s), "unit": UNIT,
+               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 3 * 8 * nb, "steps": args.e2e_steps,
+               "ms_per_step": e2e_s * 1e3 / args.e2e_steps,
+               "call": "pm_simulate_pk_host: host noise -> ICs + 6 steps + P(k) -> host P(k)"}
         d_host = torch.empty((1, 3, N), dtype=torch.float32, pin_memory=True)
         v_host = torch.empty((1, 3, N), dtype=torch.float32, pin_memory=True)
-        pm.simulate_host(noise_host, d_host, v_host)
-        if ws > 1:
-            dist.barrier()
-        te = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            pm.simulate_host(noise_host, d_host, v_host)
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - te
-        e2e_s = max_over_ranks(e2e_s, ws, dev)
-        e2e = {"value": whole_job_rate(N * cfg.n_steps * args.e2e_steps, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 4 * N,
-               "d2h_bytes_per_step": 2 * 3 * 4 * N, "steps": args.e2e_steps,
-               "ms_per_step": e2e_s * 1e3 / args.e2e_steps, "host_link_gbs": host_link_gbs(d_host)}
+        es_s = timed(lambda: pm.simulate_host(noise_host, d_host, v_host))
+        e2e_state = {"value": whole_job_rate(N * cfg.n_steps * args.e2e_steps, ws, es_s), "unit": UNIT,
+                     "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 2 * 3 * 4 * N, "steps": args.e2e_steps,
+                     "ms_per_step": es_s * 1e3 / args.e2e_steps,
+                     "call": "pm_simulate_host: host noise -> ICs + 6 steps -> host disp, vel (no P(k))",
+                     "host_link_gbs": host_link_gbs(d_host)}
 
     # roofline of the dominant kernel (largest share of the timed region)
     alg = algorithmic_bytes(n, cfg.n_mesh, cfg.n_steps)
@@ -632,7 +647,7 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": WORKLOAD, "roofline": roof, "kernels": kernels, "gpu_launches": int(launches),
-            "e2e": e2e,
+            "e2e": e2e, "e2e_state": e2e_state,
             "clocks": clock_info,
             "ms_per_pm_step": ms / args.steps / cfg.n_steps}
     if not args.no_extra:

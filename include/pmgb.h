@@ -240,6 +240,15 @@ int pm_profile_read(pm_handle* h, double* ms, int64_t* calls, int64_t* launches,
  * first call (owned by the handle).  Synchronises the stream. */
 int pm_simulate_host(pm_handle* h, const float* noise, float* disp, float* vel);
 
+/* The whole analysis step from HOST buffers: copies noise [slot][N] from host
+ * memory, computes the Zel'dovich (or 2LPT) ICs, all n_steps steps and the
+ * binned power spectrum of the final positions (as pm_power_spectrum: n_mesh,
+ * n_bins, HOST outputs k, pk, n_modes [slot][n_bins]).  The particle state stays
+ * on the device in the handle's buffers (shared with pm_simulate_host; allocated
+ * on the first call of either).  Synchronises the stream. */
+int pm_simulate_pk_host(pm_handle* h, const float* noise, int32_t n_mesh, int32_t n_bins, double* k, double* pk,
+                        int64_t* n_modes);
+
 /* Largest mesh pm_power_spectrum_static accepts (cells per dimension). */
 #define PM_STATIC_PK_MAX_MESH 64
 

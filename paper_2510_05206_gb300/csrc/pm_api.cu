@@ -1142,9 +1142,10 @@ int pm_profile_read(pm_handle* h, double* ms, int64_t* calls, int64_t* launches,
     return PM_OK;
 }
 
-int pm_simulate_host(pm_handle* h, const float* noise, float* disp, float* vel) {
-    if (!h) return PM_ERR_ARG;
-    if (!noise || !disp || !vel) return h->fail(PM_ERR_ARG, "pm_simulate_host: NULL buffer");
+namespace {
+// host-buffer modes: upload the noise, ICs and the whole run into the handle's
+// device state buffers (allocated on first use)
+int host_mode_run(pm_handle* h, const float* noise) {
     int rc;
     const size_t Nb = (size_t)h->Np() * h->B;
     if (!h->d_noise) {
@@ -1152,11 +1153,32 @@ int pm_simulate_host(pm_handle* h, const float* noise, float* disp, float* vel) 
         if ((rc = dalloc(h, &h->d_disp, 3 * Nb, "host-mode disp"))) return rc;
         if ((rc = dalloc(h, &h->d_vel, 3 * Nb, "host-mode vel"))) return rc;
     }
-    cudaStream_t st = h->stream;
-    if (cudaMemcpyAsync(h->d_noise, noise, Nb * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (cudaMemcpyAsync(h->d_noise, noise, Nb * 4, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return h->fail(PM_ERR_CUDA, "noise upload");
     if ((rc = ic_impl(h, h->d_noise, h->d_disp, h->d_vel, h->B))) return rc;
-    if ((rc = pm_run(h, h->d_disp, h->d_vel, 0, (int)h->table.size()))) return rc;
+    return pm_run(h, h->d_disp, h->d_vel, 0, (int)h->table.size());
+}
+}  // namespace
+
+int pm_simulate_pk_host(pm_handle* h, const float* noise, int32_t n_mesh, int32_t n_bins, double* k, double* pk,
+                        int64_t* n_modes) {
+    if (!h) return PM_ERR_ARG;
+    if (!noise || !k || !pk || !n_modes) return h->fail(PM_ERR_ARG, "pm_simulate_pk_host: NULL buffer");
+    if (!pow2_in_range(n_mesh) || n_mesh > h->npk)
+        return h->fail(PM_ERR_ARG, "P(k) mesh %d must be a power of two in [16, %d]", n_mesh, h->npk);
+    if (n_bins < 1 || n_bins > n_mesh) return h->fail(PM_ERR_ARG, "n_bins must be in [1, %d]", n_mesh);
+    int rc;
+    if ((rc = host_mode_run(h, noise))) return rc;
+    return pm_power_spectrum(h, h->d_disp, n_mesh, n_bins, k, pk, n_modes);
+}
+
+int pm_simulate_host(pm_handle* h, const float* noise, float* disp, float* vel) {
+    if (!h) return PM_ERR_ARG;
+    if (!noise || !disp || !vel) return h->fail(PM_ERR_ARG, "pm_simulate_host: NULL buffer");
+    int rc;
+    const size_t Nb = (size_t)h->Np() * h->B;
+    cudaStream_t st = h->stream;
+    if ((rc = host_mode_run(h, noise))) return rc;
     if (cudaMemcpyAsync(disp, h->d_disp, 3 * Nb * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(vel, h->d_vel, 3 * Nb * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return h->fail(PM_ERR_CUDA, "state download");

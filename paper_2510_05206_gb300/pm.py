@@ -262,6 +262,25 @@ class PM:
                                               ctypes.c_void_p(disp.data_ptr()), ctypes.c_void_p(vel.data_ptr())))
         return disp, vel
 
+    def simulate_pk_host(self, noise, n_mesh=None, n_bins=None):
+        """noise: host float32 array/tensor [B, N] (pinned for full speed).  ICs, the
+        whole run and the power spectrum of the final positions; returns host
+        (k, P, counts) [B, n_bins].  The state stays in the handle's device buffers."""
+        if isinstance(noise, np.ndarray):
+            noise = torch.from_numpy(np.ascontiguousarray(noise, dtype=np.float32))
+        if noise.is_cuda or noise.dtype != torch.float32 or not noise.is_contiguous() or \
+                noise.numel() != self.B * self.N:
+            raise ValueError(f"noise must be a contiguous float32 host tensor of {self.B} x {self.N} values")
+        n = n_mesh or (self.cfg.pk_mesh_max or self.cfg.n_mesh)
+        nb = n_bins or n // 2
+        k, pk = np.zeros((self.B, nb)), np.zeros((self.B, nb))
+        cnt = np.zeros((self.B, nb), dtype=np.int64)
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._stream()
+        self._check(self.lib.pm_simulate_pk_host(self.h, ctypes.c_void_p(noise.data_ptr()), int(n), int(nb), dptr(k),
+                                                 dptr(pk), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return k, pk, cnt
+
 
 def power_spectrum_static(disp, n_part, box, n_mesh, n_bins, stream=None):
     """pm_power_spectrum_static: P(k) of one simulation without any device

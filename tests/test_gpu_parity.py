@@ -307,6 +307,23 @@ def test_simulate_host_matches_device_path():
     assert _disp_err(dh[0].double().numpy(), _np(d)[0]) < 1e-5
 
 
+def test_simulate_pk_host_matches_device_path():
+    # the whole analysis step from host noise to host P(k) equals ICs + run + P(k)
+    # on device buffers (same kernels, same inputs)
+    n, L = 32, 256.0
+    pm = PM(Config(n_part=n, n_mesh=n, box=L), device=DEV)
+    w = inputs.white_noise(n, seed=10).reshape(1, -1).astype(np.float32)
+    kh, pkh, ch = pm.simulate_pk_host(torch.from_numpy(w).pin_memory(), 32, 16)
+    d, v = pm.ic_zeldovich(_t(w))
+    pm.run(d, v)
+    k, pk, c = pm.power_spectrum(d, 32, 16)
+    np.testing.assert_array_equal(ch, c)
+    np.testing.assert_array_equal(kh, k)
+    assert np.max(np.abs(pkh / pk - 1)) < 1e-5
+    with pytest.raises(ValueError):
+        pm.simulate_pk_host(_t(w))          # device tensor: not a host buffer
+
+
 def test_step_table_matches_oracle():
     pm = PM(Config(n_part=16, n_mesh=16, box=100.0, n_steps=7), device=DEV)
     ref = cosmology.step_table(cosmology.Growth(0.3), 0.02, 1.0, 7)
