@@ -214,7 +214,6 @@ struct ZArgs {
     const float* grad1;       // Im of the 1D gradient kernel per bin, 0 on the Nyquist bin
     const float* dec1;        // deconvolution 1 / W^(k)^2 per bin of one axis, or NULL
     const float* ictab;       // IC: sqrt(P(k) M / L^3) / (D(1) k^2) / M per integer k^2 index (0 if masked)
-    const int* bintab;        // P(k): bin of each integer k^2 index (-1 = none)
     double* pk_out;           // P(k): [slot][3][nbins] (sum w|d|^2, sum w|k|, sum w)
     int nbins;
     float scale;              // overall factor of the multiplier
@@ -223,6 +222,20 @@ struct ZArgs {
 
 enum { Z_FORCE = 0, Z_FORCE_IL = 1, Z_IC = 2, Z_PK = 3, Z_ADJ = 4, Z_IC_ADJ = 5, Z_POT = 6, Z_POT_IL = 7,
        Z_IC_D2 = 8, Z_IC_O2 = 9, Z_LPT2 = 10, Z_PKX = 11, Z_DEC = 16 };
+
+// Last-stage store of the IC z pass: column l of the inverse transform G goes to
+// the x and y displacement spectra as i kx G and i my G.
+struct IcXYStore {
+    float2* ox;
+    float2* oy;
+    long long es;
+    int kx0;
+    float my;
+    __device__ __forceinline__ void operator()(int l, int e, float2 v) const {
+        ox[e * es + l] = cmul_i(cscale(v, (float)(kx0 + l)), 1);
+        oy[e * es + l] = cmul_i(cscale(v, my), 1);
+    }
+};
 
 // MODE_DEC = mode | Z_DEC: the mode's multiplier also divides by the squared mass
 // assignment kernel (deconvolution tables in a.dec1), compiled only where used.
@@ -294,7 +307,11 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
 #pragma unroll
                 for (int k = 0; k < CH; ++k) {
                     const int e = e0 + k, mz = freq_index(e, n);
-                    const int bk = __ldg(&a.bintab[kxy + mz * mz]);
+                    // bin floor(|m| - 1/2) of the integer |m|^2 <= 3 (n/2)^2 < 2^24: the float
+                    // square root is correctly rounded and |m| never lies within 1e-4 of a
+                    // bin edge, so this equals the exact bin (0 for |m| = 0 gives -1)
+                    int bk = (int)floorf(sqrtf((float)(kxy + mz * mz)) - 0.5f);
+                    bk = bk < a.nbins ? bk : -1;
                     const float2 d = A(l, e);
                     const float2 dt = MODE == Z_PKX ? A2(l, e) : d;
                     if (bk != cur) {
@@ -438,6 +455,20 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
         return;
     }
 
+    if constexpr (MODE == Z_IC) {
+        // psi1_c^ = i m_c (kf T w^) with A = kf T w^: along a z column m_x and m_y are
+        // constants, so the x and y components are i kx and i my times ONE inverse
+        // transform of A (two stores from its last stage); z needs its own
+        const IcXYStore sxy{a.out[0] + off, a.out[1] + off, ES, kx0, (float)my};
+        fft_io<n, COL_TILE, 1, false, false>(A, sxy, B, tw, 1);
+        __syncthreads();
+        auto mult_z = [&](int l, int e) -> float2 {
+            return cmul_i(cscale(A(l, e), (float)freq_index(e, n)), 1);
+        };
+        fft_io<n, COL_TILE, 1, false, false>(mult_z, GCols{a.out[2] + off, ES}, B, tw, 1);
+        return;
+    }
+
     const int ncomp = MODE == Z_FORCE_IL ? 6 : 3;
     for (int c = 0; c < ncomp; ++c) {
         const int axis = c % 3;
@@ -446,11 +477,6 @@ __global__ void __launch_bounds__(1 << LOG2N, col_min_blocks(LOG2N)) k_fft_z(ZAr
             float2 r = make_float2(0.f, 0.f);
             if (kx > n / 2) return r;
             const int mz = freq_index(e, n);
-            if (MODE == Z_IC) {
-                // psi1_c^ = i k_c T(k^2) w^ (A holds kf T w^, zero on every Nyquist plane)
-                const int mc = axis == 0 ? kx : (axis == 1 ? my : mz);
-                return cmul_i(cscale(A(l, e), (float)mc), 1);
-            }
             if (MODE == Z_IC_D2 || MODE == Z_IC_O2) {
                 // second derivatives of psi1 for the 2LPT source (Eq. LPT_kernels):
                 // psi1_i,j^ = i k_j psi1_i^ = -k_i k_j T(k^2) w^; D2: (xx, yy, zz), O2: (xy, xz, yz)
@@ -656,7 +682,6 @@ int pm_fft_z(int log2n, int mode, const PmZPass& p, int nslots, cudaStream_t st)
     a.grad1 = p.grad1;
     a.dec1 = p.dec1;
     a.ictab = p.ictab;
-    a.bintab = p.bintab;
     a.pk_out = p.pk_out;
     a.nbins = p.nbins;
     a.scale = p.scale;

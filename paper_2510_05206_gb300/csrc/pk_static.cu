@@ -5,8 +5,8 @@
 // whose host application owns every device allocation, or processes running
 // under a fixed device-memory budget that is already committed.  For them this
 // file offers one entry point, pm_power_spectrum_static, that needs no handle
-// and allocates nothing: its scratch (density mesh, half spectrum, twiddles,
-// bin table and FP64 bin sums) lives in one file-scope __device__ array of
+// and allocates nothing: its scratch (density mesh, half spectrum, twiddles
+// and FP64 bin sums) lives in one file-scope __device__ array of
 // fixed size, which every GPU that loads the library holds until the process
 // exits.  The kernels are the same deposit / FFT / binning kernels the
 // handle-based pm_power_spectrum launches.
@@ -22,7 +22,6 @@ constexpr int kMaxMesh = PM_STATIC_PK_MAX_MESH;
 constexpr int kMaxBins = PM_STATIC_PK_MAX_MESH / 2;
 constexpr long long kMeshFloats = (long long)kMaxMesh * kMaxMesh * kMaxMesh;
 constexpr long long kSpecCplx = (long long)kMaxMesh * kMaxMesh * (kMaxMesh / 2 + SPEC_PAD);
-constexpr int kBinTab = 3 * (kMaxMesh / 2) * (kMaxMesh / 2) + 1;
 
 // byte offsets inside the scratch array (each 256-byte aligned); the FP64 bin
 // accumulators hold sum w |rho^|^2 per bin
@@ -30,8 +29,7 @@ constexpr long long align256(long long b) { return (b + 255) / 256 * 256; }
 constexpr long long kOffRho = 0;
 constexpr long long kOffSpec = align256(kOffRho + 4 * kMeshFloats);
 constexpr long long kOffTw = align256(kOffSpec + 8 * kSpecCplx);
-constexpr long long kOffBin = align256(kOffTw + 8 * kMaxMesh);
-constexpr long long kOffAcc = align256(kOffBin + 4 * kBinTab);
+constexpr long long kOffAcc = align256(kOffTw + 8 * kMaxMesh);
 constexpr long long kOffCoef = align256(kOffAcc + 8 * kMaxBins);
 constexpr long long kScratchBytes = align256(kOffCoef + (long long)sizeof(SlotCoef));
 
@@ -41,16 +39,12 @@ static __device__ __align__(256) unsigned char g_pk_scratch[kScratchBytes];
 std::mutex g_mu;
 void* g_addr[64] = {};
 
-// twiddles exp(-2 pi i m / n), the bin of every integer |m|^2 and the unit coefficient
-__global__ void k_static_tables(float2* tw, int n, int* bintab, int ns, int nbins, SlotCoef* coef) {
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < ns; m += gridDim.x * blockDim.x) {
-        if (m < n) {
-            double s, c;
-            sincospi(2.0 * m / n, &s, &c);
-            tw[m] = make_float2((float)c, (float)-s);
-        }
-        const int b = (int)floor(sqrt((double)m) - 0.5);
-        bintab[m] = (m > 0 && b >= 0 && b < nbins) ? b : -1;
+// twiddles exp(-2 pi i m / n) and the unit coefficient
+__global__ void k_static_tables(float2* tw, int n, SlotCoef* coef) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * m / n, &s, &c);
+        tw[m] = make_float2((float)c, (float)-s);
         if (m == 0) {
             SlotCoef u{};
             u.active = 1;
@@ -95,7 +89,6 @@ extern "C" int pm_power_spectrum_static(const float* disp, int32_t n_part, doubl
     float* rho = reinterpret_cast<float*>(s + kOffRho);
     float2* spec = reinterpret_cast<float2*>(s + kOffSpec);
     float2* tw = reinterpret_cast<float2*>(s + kOffTw);
-    int* bintab = reinterpret_cast<int*>(s + kOffBin);
     double* acc = reinterpret_cast<double*>(s + kOffAcc);
     SlotCoef* coef = reinterpret_cast<SlotCoef*>(s + kOffCoef);
 
@@ -103,12 +96,11 @@ extern "C" int pm_power_spectrum_static(const float* disp, int32_t n_part, doubl
     const int n = n_mesh, l2 = ilog2s(n);
     const long long M = (long long)n * n * n;
     const long long S = (long long)n * n * (n / 2 + SPEC_PAD);
-    const int ns = 3 * (n / 2) * (n / 2) + 1;
     // the array keeps the previous call's contents: clear what accumulates
     cudaMemsetAsync(rho, 0, sizeof(float) * M, st);
     cudaMemsetAsync(spec, 0, sizeof(float2) * S, st);
     cudaMemsetAsync(acc, 0, sizeof(double) * n_bins, st);
-    k_static_tables<<<(ns + 255) / 256, 256, 0, st>>>(tw, n, bintab, ns, n_bins, coef);
+    k_static_tables<<<(n + 255) / 256, 256, 0, st>>>(tw, n, coef);
     PmGeom g;
     g.log2np = ilog2s(n_part);
     g.log2ng = l2;
@@ -122,7 +114,6 @@ extern "C" int pm_power_spectrum_static(const float* disp, int32_t n_part, doubl
     z.in[0] = spec;
     z.slot_stride = S;
     z.tw = tw;
-    z.bintab = bintab;
     z.pk_out = acc;
     z.nbins = n_bins;
     pm_fft_z(l2, PM_Z_PK, z, 1, st);

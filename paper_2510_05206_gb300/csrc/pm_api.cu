@@ -61,7 +61,6 @@ struct pm_handle {
     double* d_pk = nullptr;      // [B][pk_bins_cap]: sum over each bin of w |rho^|^2
     int pk_bins_cap = 0;
     struct BinTable {
-        int* d_tab = nullptr;                       // bin of every integer |m|^2 (-1 = none)
         std::vector<double> count, ksum;            // exact per-bin mode counts and sum |m|
     };
     std::map<std::pair<int, int>, BinTable> bintabs;   // (n, nbins)
@@ -348,6 +347,8 @@ int bintab_for(pm_handle* h, int n, int nbins, const pm_handle::BinTable** out) 
     auto key = std::make_pair(n, nbins);
     auto it = h->bintabs.find(key);
     if (it != h->bintabs.end()) { *out = &it->second; return PM_OK; }
+    // bin floor(|m| - 1/2) of each integer |m|^2 (the z pass takes the same bin in
+    // float arithmetic, which is exact for |m|^2 < 2^24)
     const int ns = 3 * (n / 2) * (n / 2) + 1;
     std::vector<int> t(ns);
     for (int s = 0; s < ns; ++s) {
@@ -373,10 +374,6 @@ int bintab_for(pm_handle* h, int n, int nbins, const pm_handle::BinTable** out) 
             }
         }
     }
-    int rc = dalloc(h, &bt.d_tab, ns, "P(k) bin table");
-    if (rc) return rc;
-    if (cudaMemcpy(bt.d_tab, t.data(), ns * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
-        return h->fail(PM_ERR_CUDA, "upload bin table");
     auto res = h->bintabs.emplace(key, std::move(bt));
     *out = &res.first->second;
     return PM_OK;
@@ -653,7 +650,6 @@ void pm_destroy(pm_handle* h) {
     cudaFree(h->d_dec);
     cudaFree(h->d_ictab);
     cudaFree(h->d_pk);
-    for (auto& kv : h->bintabs) cudaFree(kv.second.d_tab);
     cudaFree(h->adj3);
     cudaFree(h->jrho);
     cudaFree(h->jforce);
@@ -836,7 +832,6 @@ int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n, int32_t nbins,
     z.in[0] = h->spec;
     z.slot_stride = h->spec_slot();
     z.tw = h->d_tw[l2];
-    z.bintab = bt->d_tab;
     z.pk_out = h->d_pk;
     z.nbins = nbins;
     pm_fft_z(l2, PM_Z_PK, z, h->B, st);
@@ -893,7 +888,6 @@ int pm_power_spectrum_jvp(pm_handle* h, const float* disp, const float* tdisp, i
     z.in[1] = h->spec + S;
     z.slot_stride = h->spec_slot();
     z.tw = h->d_tw[l2];
-    z.bintab = bt->d_tab;
     z.pk_out = h->d_pk;
     z.nbins = nbins;
     pm_fft_z(l2, PM_Z_PKX, z, h->B, st);

@@ -14,7 +14,6 @@ struct PmZPass {
     const float* grad1;
     const float* dec1;      // 1 / W^(k)^2 per DFT bin of one axis (deconvolution), or NULL
     const float* ictab;
-    const int* bintab;
     double* pk_out;         // P(k): [slot][nbins] sums of w |delta^|^2
     int nbins;
     float scale;

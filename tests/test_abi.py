@@ -69,3 +69,14 @@ def test_host_step_table_matches_oracle(lib, stepper, time_var, om):
     g = cosmology.Growth(om)
     ref = cosmology.step_table(g, 0.02, 1.0, 10, ["bullfrog", "fastpm"][stepper], ["D", "a"][time_var])
     np.testing.assert_allclose(out, ref, rtol=1e-9, atol=1e-12)
+
+
+def test_float32_bin_rule_equals_fp64_for_every_mesh_mode():
+    # The P(k) z pass takes each mode's bin as floor(sqrt(|m|^2) - 1/2) in float32
+    # (correctly rounded square root); the oracle bins |k| / k_F in FP64.  Every
+    # integer |m|^2 that a mesh of up to 1024^3 cells reaches (<= 3 * 512^2) gets the
+    # same bin in both precisions: no |m| lies close enough to a bin edge.
+    s = np.arange(0, 3 * 512 * 512 + 1)
+    b32 = np.floor(np.sqrt(s.astype(np.float32)) - np.float32(0.5)).astype(np.int64)
+    b64 = np.floor(np.sqrt(s.astype(np.float64)) - 0.5).astype(np.int64)
+    np.testing.assert_array_equal(b32, b64)
