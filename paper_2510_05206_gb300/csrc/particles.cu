@@ -223,7 +223,7 @@ template <int ORDER>
 struct DepWindow {
     static constexpr int LO = ORDER >= 3 ? 1 : 0;   // taps below the base cell
     static constexpr int HALO = ORDER == 4 ? 2 : DEP_HALO;   // PCS: 4 taps leave room for 2
-    static constexpr int WX = 44;                   // 32 + 2 halo + ORDER - 1 + alignment slack, rounded to 4
+    static constexpr int WX = 64;                   // >= 32 + 2 halo + ORDER - 1 + alignment slack; a multiple of 32
     static constexpr int WY = 16;                   // 8 + 2 halo + ORDER - 1, rounded up
     static constexpr int WZ = 16;
     static constexpr int QX = WX / 4;               // 16-byte groups per window row
