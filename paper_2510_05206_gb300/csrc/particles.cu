@@ -221,8 +221,8 @@ constexpr float DEP_UNFIX = 1.f / 1048576.f;
 
 template <int ORDER>
 struct DepWindow {
-    static constexpr int LO = ORDER >= 3 ? 1 : 0;   // taps below the base cell
-    static constexpr int HALO = ORDER == 4 ? 2 : DEP_HALO;   // PCS: 4 taps leave room for 2
+    static constexpr int LO = ORDER == 5 ? 2 : (ORDER >= 3 ? 1 : 0);   // taps below the base cell
+    static constexpr int HALO = ORDER >= 4 ? 2 : DEP_HALO;   // PCS (4 taps) and ES (5) leave room for 2
     static constexpr int WX = 64;                   // >= 32 + 2 halo + ORDER - 1 + alignment slack; a multiple of 32
     static constexpr int WY = 16;                   // 8 + 2 halo + ORDER - 1, rounded up
     static constexpr int WZ = 16;
@@ -1228,7 +1228,7 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
     const long long N = 1ll << (3 * g.log2np);
     const int R = 1 << (g.log2ng - g.log2np > 0 ? g.log2ng - g.log2np : 0);
     const bool tiled = (g.log2ng - g.log2np == 0 && g.log2np >= 5) || (g.log2ng - g.log2np == 1 && g.log2np >= 4);
-    if (tiled && order >= 2 && order <= 4) {
+    if (tiled && order >= 2 && order <= 5) {
         const int np = 1 << g.log2np;
         const unsigned ntiles = (unsigned)((long long)(np / (32 / R)) * (np / (8 / R)) * (np / (8 / R)));
 #define PM_DT(O, RR)                                                                                        \
@@ -1253,8 +1253,10 @@ int pm_deposit(int order, const PmGeom& g, const float* disp, const float* vel, 
         else if (order == 2) PM_DT(2, 2)
         else if (order == 3 && R == 1) PM_DT(3, 1)
         else if (order == 3) PM_DT(3, 2)
-        else if (R == 1) PM_DT(4, 1)
-        else PM_DT(4, 2)
+        else if (order == 4 && R == 1) PM_DT(4, 1)
+        else if (order == 4) PM_DT(4, 2)
+        else if (R == 1) PM_DT(5, 1)
+        else PM_DT(5, 2)
 #undef PM_DT
         return 0;
     }
