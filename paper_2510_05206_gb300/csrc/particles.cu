@@ -555,6 +555,18 @@ __global__ void __launch_bounds__(256, 3) k_interp_col(PmGeom g, float* __restri
         prefetch_l2(vy + ip);
         prefetch_l2(vz + ip);
     }
+    // and of the force rows that tile's undisplaced cells (+1 cell) cover: 10 x 10
+    // rows of 6 128-byte lines (8 float4 cells each), so that the walk's first
+    // touches of force lines hit L2
+    if (blockIdx.x + STATE_TILES < gridDim.x) {
+        const TG Tn(blockIdx.x + STATE_TILES, l2);
+        for (int r = threadIdx.x; r < 10 * 10 * 6; r += 256) {
+            const int zr = r / 60, yr = (r / 6) % 10, seg = r % 6;
+            const int z = (Tn.iz0 - 1 + zr) & msk, y = (Tn.iy0 - 1 + yr) & msk;
+            const int x = ((Tn.ix0 >> 3) - 1 + seg) & (msk >> 3);   // line index along the row
+            prefetch_l2(f + ((z << (2 * l2)) + (y << l2) + (x << 3)));
+        }
+    }
     float4 P[ORDER][ORDER][ORDER];   // [z plane][y][x] taps of the previous particle
 #pragma unroll
     for (int k = 0; k < ORDER; ++k)
