@@ -163,6 +163,21 @@ int pm_step_slots(pm_handle* h, float* disp, float* vel);
 int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n_mesh, int32_t n_bins, double* k, double* pk,
                       int64_t* n_modes);
 
+/* pm_power_spectrum in two halves, for callers that keep the GPU busy while
+ * results travel.  pm_power_spectrum_async enqueues the deposit, transform and
+ * binning on the handle's stream and returns without synchronising: bin_sums is
+ * a DEVICE array [slot][n_bins] (caller-owned) that receives, per bin, the FP64
+ * sum over its modes of w |rho^_k|^2 (w = 2 for the half-spectrum modes that
+ * stand for +-k).  The work is stream-ordered: bin_sums is complete once the
+ * stream has passed it (an event recorded after the call, or any later
+ * synchronisation).
+ * pm_power_spectrum_finish turns a HOST copy of those sums into the outputs of
+ * pm_power_spectrum (k, pk, n_modes, host arrays [slot][n_bins]); it launches
+ * nothing and does not touch the device. */
+int pm_power_spectrum_async(pm_handle* h, const float* disp, int32_t n_mesh, int32_t n_bins, double* bin_sums);
+int pm_power_spectrum_finish(pm_handle* h, int32_t n_mesh, int32_t n_bins, const double* bin_sums, double* k,
+                             double* pk, int64_t* n_modes);
+
 /* Forward mode of pm_power_spectrum: with the tangent tdisp of disp, dpk[slot][bin]
  * = (L^3/M^2) <2 Re(conj(delta^) delta'^)> over the bin's modes (delta' the CIC
  * density tangent of X = q + disp along tdisp, times M/N); k, pk, n_modes as

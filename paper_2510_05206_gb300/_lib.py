@@ -54,6 +54,9 @@ _SIGS = {
                                         POINTER(c_double), POINTER(c_double), POINTER(c_int64)]),
     "pm_ic_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
     "pm_density_vjp": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
+    "pm_power_spectrum_async": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
+    "pm_power_spectrum_finish": (c_int32, [c_void_p, c_int32, c_int32, POINTER(c_double), POINTER(c_double),
+                                           POINTER(c_double), POINTER(c_int64)]),
     "pm_simulate_pk_host": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, POINTER(c_double),
                                       POINTER(c_double), POINTER(c_int64)]),
     "pm_power_spectrum_static": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_int32, c_void_p,

@@ -803,27 +803,24 @@ int pm_step_slots(pm_handle* h, float* disp, float* vel) {
     return one_step(h, disp, vel, h->d_slots, 1);
 }
 
-int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n, int32_t nbins, double* k, double* pk,
-                      int64_t* nmodes) {
-    if (!h) return PM_ERR_ARG;
-    if (!disp || !k || !pk || !nmodes) return h->fail(PM_ERR_ARG, "pm_power_spectrum: NULL buffer");
+namespace {
+int pk_check(pm_handle* h, int32_t n, int32_t nbins) {
     if (!pow2_in_range(n) || n > h->npk)
         return h->fail(PM_ERR_ARG, "P(k) mesh %d must be a power of two in [16, %d]", n, h->npk);
     if (nbins < 1 || nbins > n) return h->fail(PM_ERR_ARG, "n_bins must be in [1, %d]", n);
+    return PM_OK;
+}
+
+// deposit, forward transform and binning of every slot; the FP64 sums over each
+// bin of w |rho^|^2 land in sums [slot][nbins] (device), asynchronously
+int pk_enqueue(pm_handle* h, const float* disp, int32_t n, int32_t nbins, double* sums) {
     int rc;
-    if (nbins > h->pk_bins_cap) {
-        cudaFree(h->d_pk);
-        h->d_pk = nullptr;
-        if ((rc = dalloc(h, &h->d_pk, (size_t)h->B * nbins, "P(k) bins"))) return rc;
-        h->pk_bins_cap = nbins;
-    }
     const pm_handle::BinTable* bt = nullptr;
     if ((rc = bintab_for(h, n, nbins, &bt))) return rc;
     cudaStream_t st = h->stream;
     const int l2 = ilog2i(n);
-    const long long M = mesh_elems(n);
     cudaMemsetAsync(h->rho, 0, sizeof(float) * h->rho_slot() * h->B, st);
-    cudaMemsetAsync(h->d_pk, 0, sizeof(double) * h->B * nbins, st);
+    cudaMemsetAsync(sums, 0, sizeof(double) * h->B * nbins, st);
     h->phase(8, 4);
     pm_deposit(2, geom(h, n, h->rho_slot()), disp, nullptr, h->d_unit, 0, 0.f, h->rho, h->B, st);
     pm_fft_r2c_x(l2, h->rho, h->rho_slot(), h->spec, h->spec_slot(), h->B, h->d_tw[l2], st);
@@ -832,15 +829,19 @@ int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n, int32_t nbins,
     z.in[0] = h->spec;
     z.slot_stride = h->spec_slot();
     z.tw = h->d_tw[l2];
-    z.pk_out = h->d_pk;
+    z.pk_out = sums;
     z.nbins = nbins;
     pm_fft_z(l2, PM_Z_PK, z, h->B, st);
     h->phase_end();
-    if ((rc = h->check_launch("power spectrum"))) return rc;
-    std::vector<double> acc((size_t)h->B * nbins);
-    if (cudaMemcpyAsync(acc.data(), h->d_pk, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return h->fail(PM_ERR_CUDA, "power spectrum readback: %s", cudaGetErrorString(cudaGetLastError()));
+    return h->check_launch("power spectrum");
+}
+
+// k, P(k) and mode counts from the bin sums (host arithmetic only)
+int pk_finish(pm_handle* h, int32_t n, int32_t nbins, const double* acc, double* k, double* pk, int64_t* nmodes) {
+    int rc;
+    const pm_handle::BinTable* bt = nullptr;
+    if ((rc = bintab_for(h, n, nbins, &bt))) return rc;
+    const long long M = mesh_elems(n);
     const double L = h->cfg.box, kf = 2.0 * M_PI / L;
     const double MN = (double)M / (double)h->Np();            // delta^ = (M/N) rho^ for k != 0
     for (int b = 0; b < h->B; ++b) {
@@ -853,6 +854,45 @@ int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n, int32_t nbins,
         }
     }
     return PM_OK;
+}
+}  // namespace
+
+int pm_power_spectrum(pm_handle* h, const float* disp, int32_t n, int32_t nbins, double* k, double* pk,
+                      int64_t* nmodes) {
+    if (!h) return PM_ERR_ARG;
+    if (!disp || !k || !pk || !nmodes) return h->fail(PM_ERR_ARG, "pm_power_spectrum: NULL buffer");
+    int rc;
+    if ((rc = pk_check(h, n, nbins))) return rc;
+    if (nbins > h->pk_bins_cap) {
+        cudaFree(h->d_pk);
+        h->d_pk = nullptr;
+        if ((rc = dalloc(h, &h->d_pk, (size_t)h->B * nbins, "P(k) bins"))) return rc;
+        h->pk_bins_cap = nbins;
+    }
+    if ((rc = pk_enqueue(h, disp, n, nbins, h->d_pk))) return rc;
+    std::vector<double> acc((size_t)h->B * nbins);
+    cudaStream_t st = h->stream;
+    if (cudaMemcpyAsync(acc.data(), h->d_pk, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return h->fail(PM_ERR_CUDA, "power spectrum readback: %s", cudaGetErrorString(cudaGetLastError()));
+    return pk_finish(h, n, nbins, acc.data(), k, pk, nmodes);
+}
+
+int pm_power_spectrum_async(pm_handle* h, const float* disp, int32_t n_mesh, int32_t n_bins, double* bin_sums) {
+    if (!h) return PM_ERR_ARG;
+    if (!disp || !bin_sums) return h->fail(PM_ERR_ARG, "pm_power_spectrum_async: NULL buffer");
+    int rc;
+    if ((rc = pk_check(h, n_mesh, n_bins))) return rc;
+    return pk_enqueue(h, disp, n_mesh, n_bins, bin_sums);
+}
+
+int pm_power_spectrum_finish(pm_handle* h, int32_t n_mesh, int32_t n_bins, const double* bin_sums, double* k,
+                             double* pk, int64_t* n_modes) {
+    if (!h) return PM_ERR_ARG;
+    if (!bin_sums || !k || !pk || !n_modes) return h->fail(PM_ERR_ARG, "pm_power_spectrum_finish: NULL buffer");
+    int rc;
+    if ((rc = pk_check(h, n_mesh, n_bins))) return rc;
+    return pk_finish(h, n_mesh, n_bins, bin_sums, k, pk, n_modes);
 }
 
 namespace {

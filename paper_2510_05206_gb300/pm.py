@@ -166,6 +166,31 @@ class PM:
             pk.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return k, pk, cnt
 
+    def power_spectrum_async(self, disp, bin_sums, n_mesh=None, n_bins=None):
+        """Enqueue P(k) without synchronising: bin_sums, a float64 CUDA tensor of
+        B x n_bins values, receives the raw per-bin sums (see power_spectrum_finish)."""
+        n = n_mesh or (self.cfg.pk_mesh_max or self.cfg.n_mesh)
+        nb = n_bins or n // 2
+        if not (bin_sums.is_cuda and bin_sums.dtype == torch.float64 and bin_sums.is_contiguous()
+                and bin_sums.numel() == self.B * nb):
+            raise ValueError(f"bin_sums must be a contiguous float64 CUDA tensor of {self.B} x {nb} values")
+        self._stream()
+        self._check(self.lib.pm_power_spectrum_async(self.h, _ptr(disp), int(n), int(nb), _ptr(bin_sums)))
+
+    def power_spectrum_finish(self, bin_sums, n_mesh=None, n_bins=None):
+        """(k, P, counts) from the per-bin sums of power_spectrum_async (host copy or
+        CUDA tensor; a CUDA tensor is copied to the host, which waits for it)."""
+        n = n_mesh or (self.cfg.pk_mesh_max or self.cfg.n_mesh)
+        nb = n_bins or n // 2
+        sums = np.ascontiguousarray(bin_sums.cpu().numpy() if torch.is_tensor(bin_sums) else bin_sums,
+                                    dtype=np.float64)
+        k, pk = np.zeros((self.B, nb)), np.zeros((self.B, nb))
+        cnt = np.zeros((self.B, nb), dtype=np.int64)
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._check(self.lib.pm_power_spectrum_finish(self.h, int(n), int(nb), dptr(sums), dptr(k), dptr(pk),
+                                                      cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return k, pk, cnt
+
     def density(self, disp, n_mesh=None, order=None):
         n = n_mesh or self.cfg.n_mesh
         out = torch.empty((self.B, n, n, n), device=self.device, dtype=torch.float32)

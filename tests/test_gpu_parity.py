@@ -324,6 +324,26 @@ def test_simulate_pk_host_matches_device_path():
         pm.simulate_pk_host(_t(w))          # device tensor: not a host buffer
 
 
+def test_power_spectrum_async_matches_sync():
+    # enqueue for two states back to back, finish both after one synchronisation
+    n, L = 32, 256.0
+    pm = PM(Config(n_part=n, n_mesh=n, box=L), device=DEV)
+    w = inputs.white_noise(n, seed=14).reshape(1, -1)
+    d0, v0 = pm.ic_zeldovich(_t(w))
+    d1, v1 = d0.clone(), v0.clone()
+    pm.run(d1, v1)
+    sums = torch.empty((2, 1, 16), dtype=torch.float64, device=DEV)
+    pm.power_spectrum_async(d0, sums[0], 32, 16)
+    pm.power_spectrum_async(d1, sums[1], 32, 16)
+    torch.cuda.synchronize()
+    for i, d in enumerate((d0, d1)):
+        ka, pka, ca = pm.power_spectrum_finish(sums[i], 32, 16)
+        k, pk, c = pm.power_spectrum(d, 32, 16)
+        np.testing.assert_array_equal(ca, c)
+        np.testing.assert_array_equal(ka, k)
+        assert np.max(np.abs(pka / pk - 1)) < 1e-12
+
+
 def test_step_table_matches_oracle():
     pm = PM(Config(n_part=16, n_mesh=16, box=100.0, n_steps=7), device=DEV)
     ref = cosmology.step_table(cosmology.Growth(0.3), 0.02, 1.0, 7)
