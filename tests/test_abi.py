@@ -80,3 +80,24 @@ def test_float32_bin_rule_equals_fp64_for_every_mesh_mode():
     b32 = np.floor(np.sqrt(s.astype(np.float32)) - np.float32(0.5)).astype(np.int64)
     b64 = np.floor(np.sqrt(s.astype(np.float64)) - 0.5).astype(np.int64)
     np.testing.assert_array_equal(b32, b64)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # the product path has no CPU fallback: without the built library, loading raises
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load(tmp_path / "libpmgb.so")
+
+
+@pytest.mark.parametrize("name", ["pm_set_stream", "pm_step_table", "pm_growth", "pm_ic_zeldovich",
+                                  "pm_ic_zeldovich_slot", "pm_step", "pm_run", "pm_set_slots", "pm_step_slots",
+                                  "pm_power_spectrum", "pm_power_spectrum_async", "pm_power_spectrum_finish",
+                                  "pm_power_spectrum_jvp", "pm_density", "pm_force_mesh", "pm_interp",
+                                  "pm_adjoint", "pm_jvp", "pm_ic_adjoint", "pm_density_vjp", "pm_profile",
+                                  "pm_profile_read", "pm_simulate_host", "pm_simulate_pk_host"])
+def test_null_handle_is_an_argument_error(lib, name):
+    # every call that takes a handle rejects NULL with PM_ERR_ARG before any CUDA work
+    fn = getattr(lib, name)
+    scalar = (ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t)
+    args = [0 if t in scalar else None for t in fn.argtypes]
+    args[0] = None
+    assert fn(*args) == -1
