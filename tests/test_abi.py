@@ -47,6 +47,39 @@ def test_invalid_config_rejected(lib, field, value):
     assert lib.pm_last_error(None)
 
 
+@pytest.mark.parametrize("kw", [dict(lpt_order=3), dict(interlace=2), dict(stepper=2), dict(time_var=2),
+                                dict(lap_order=5), dict(omega_m=1.5), dict(sigma8=0.0), dict(a_ini=1e-5),
+                                dict(a_end=4.0), dict(pk_mesh_max=48), dict(nufft=2),
+                                dict(nufft=1, grad_order=4), dict(nufft=1, grad_order=0, interlace=1),
+                                dict(nufft=1, grad_order=0, deconvolve=1),
+                                dict(nufft=1, grad_order=0, n_mesh=1024),
+                                dict(n_part=1024, n_mesh=1024, batch=2)])
+def test_invalid_option_combinations_rejected(lib, kw):
+    c = Config(n_part=32, n_mesh=32)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    out = ctypes.c_size_t()
+    cc = c.to_c()
+    assert lib.pm_workspace_bytes(ctypes.byref(cc), ctypes.byref(out)) == -1
+    assert lib.pm_last_error(None)
+
+
+def test_valid_option_combinations_size_their_workspace(lib):
+    def ws(**kw):
+        c = Config(**kw).to_c()
+        out = ctypes.c_size_t()
+        assert lib.pm_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 0, lib.pm_last_error(None)
+        return out.value
+    base = ws(n_part=64, n_mesh=64)
+    # the NUFFT grid is twice the mesh per dimension: 8x the mesh workspace
+    assert ws(n_part=64, n_mesh=64, nufft=1, grad_order=0) > 4 * base
+    # an interlaced second grid doubles the meshes
+    assert ws(n_part=64, n_mesh=64, interlace=1) > 1.5 * base
+    for kw in (dict(order=4, deconvolve=1), dict(lpt_order=2), dict(stepper=1, time_var=1),
+               dict(grad_order=6, lap_order=4), dict(pk_mesh_max=128)):
+        assert ws(n_part=64, n_mesh=64, **kw) >= base
+
+
 def test_workspace_bytes_scales_with_batch(lib):
     def ws(**kw):
         c = Config(**kw).to_c()
