@@ -170,6 +170,47 @@ def host_link_gbs(host):
     return out
 
 
+def cufft_comparison(n, dev, reps=10):
+    """cuFFT (through torch.fft) on the spectral part of a PM step for comparison:
+    real-to-complex 3D transform of an n^3 mesh, Poisson multiplier, complex-to-real
+    back (the library's own passes do this as x, y forward, the fused z pass, y, x
+    inverse).  Failures are reported in the line instead of ending the run."""
+    import torch
+    try:
+        x = torch.randn(n, n, n, device=dev, dtype=torch.float32)
+        kz = torch.fft.fftfreq(n, device=dev).view(n, 1, 1)
+        ky = torch.fft.fftfreq(n, device=dev).view(1, n, 1)
+        kx = torch.fft.rfftfreq(n, device=dev).view(1, 1, n // 2 + 1)
+        k2 = kx ** 2 + ky ** 2 + kz ** 2
+        k2[0, 0, 0] = 1.0
+        green = (-1.0 / k2).to(torch.float32)
+        green[0, 0, 0] = 0.0
+
+        def chain():
+            return torch.fft.irfftn(torch.fft.rfftn(x) * green, s=(n, n, n))
+
+        for _ in range(3):
+            chain()
+        if torch.cuda.is_available() and x.is_cuda:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                chain()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        else:
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                chain()
+            ms = (time.perf_counter() - t0) * 1e3 / reps
+        del x, green, k2
+        return {"mesh": n, "ms_rfftn_green_irfftn": ms}
+    except Exception as e:  # noqa: BLE001 - a comparison must not end the benchmark
+        return {"mesh": n, "error": f"{type(e).__name__}: {e}"}
+
+
 def algorithmic_bytes(n_part, n_mesh, n_steps=6):
     """Compulsory HBM bytes per launch of each phase (float32; M = mesh cells,
     N = particles; complex half spectra count as M/2 complex = 4M bytes),
@@ -659,6 +700,10 @@ def main():
             "clocks": clock_info,
             "ms_per_pm_step": ms / args.steps / cfg.n_steps}
     if not args.no_extra:
+        cmp = cufft_comparison(cfg.n_mesh, dev)
+        cmp["ms_own_passes"] = sum(kernels[k]["ms_per_launch"] for k in
+                                   ("fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv") if k in kernels)
+        line["cufft_comparison"] = cmp
         line["adjoint"] = adjoint_benchmark(dev)
         line["scaleup"] = scaleup_benchmark(dev)
         line["deconvolve"] = deconvolve_benchmark(dev)

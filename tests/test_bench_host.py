@@ -66,3 +66,11 @@ def test_traffic_lines_parse(bench):
         v = bench.measured_traffic(k)
         assert v is None or 5e8 < v < 2e10
     assert bench.measured_traffic("no_such_kernel") is None
+
+
+def test_cufft_comparison_runs_and_reports_failures(bench):
+    import torch
+    r = bench.cufft_comparison(16, torch.device("cpu"), reps=1)
+    assert r["mesh"] == 16 and r["ms_rfftn_green_irfftn"] > 0
+    # a failure is reported in the line instead of ending the benchmark
+    assert "error" in bench.cufft_comparison(-1, torch.device("cpu"), reps=1)
